@@ -1,0 +1,164 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle tests and the bench.
+
+This module draws scenes, cameras and target images only; it contains none of
+the rasterizer's or the schedule's arithmetic, so that both implementations
+can consume identical inputs without sharing any of the method's code.
+
+Per-Gaussian parameter row (59 values), the interface both sides use:
+    0:3   mean (world)            3:6   log scale
+    6:10  quaternion (w, x, y, z) 10    opacity logit
+    11:59 SH coefficients, coefficient-major: 11 + 3*k + channel, k = l*l + l + m
+
+Scene recipes (the paper evaluates on Mip-NeRF 360, Deep Blending and
+Tanks&Temples, which are not available here; these seeded scenes stand in for
+them with the shapes and parameter distributions of the workloads):
+  * ``random_gaussians``: means U[-1,1]^3, log-scales N(-3, 0.5), random unit
+    quaternions, opacity logit N(0, 1), SH coefficients N(0, 0.2^2).
+  * ``textured_scene``: 90% of the Gaussians on 20 random planes and spheres
+    whose SH DC colour follows a seeded band-limited noise over the surface
+    coordinates, 10% on a uniform background shell of radius 12; the other
+    parameters are drawn as in ``random_gaussians``.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+NPARAM = 59
+SH_DC_NORM = 0.28209479177387814  # value of the degree-0 basis, used only to pick DC colours
+
+
+def random_gaussians(n: int, seed: int, extent: float = 1.0) -> np.ndarray:
+    """(n, 59) float64 Gaussians with the distributions of the 1k-Gaussian scene."""
+    rng = np.random.default_rng(seed)
+    g = np.zeros((n, NPARAM))
+    g[:, 0:3] = rng.uniform(-extent, extent, size=(n, 3))
+    g[:, 3:6] = rng.normal(-3.0, 0.5, size=(n, 3))
+    q = rng.normal(size=(n, 4))
+    g[:, 6:10] = q / np.linalg.norm(q, axis=1, keepdims=True)
+    g[:, 10] = rng.normal(0.0, 1.0, size=n)
+    g[:, 11:59] = rng.normal(0.0, 0.2, size=(n, 48))
+    return g
+
+
+def look_at(eye, target=(0.0, 0.0, 0.0), up=(0.0, 0.0, 1.0)) -> np.ndarray:
+    """World-to-camera [R|t] (3x4) of a camera at ``eye`` looking at ``target``
+    (x right, y down, z forward)."""
+    eye = np.asarray(eye, float)
+    fwd = np.asarray(target, float) - eye
+    fwd /= np.linalg.norm(fwd)
+    right = np.cross(fwd, np.asarray(up, float))
+    if np.linalg.norm(right) < 1e-9:
+        right = np.cross(fwd, np.array([0.0, 1.0, 0.0]))
+    right /= np.linalg.norm(right)
+    down = np.cross(fwd, right)
+    R = np.stack([right, down, fwd])  # rows: camera axes in world coordinates
+    t = -R @ eye
+    return np.concatenate([R, t[:, None]], axis=1)
+
+
+def intrinsics(width: int, height: int, fov_x_deg: float = 60.0):
+    """(fx, fy, cx, cy) of a pinhole with square pixels and centred principal point."""
+    fx = 0.5 * width / math.tan(math.radians(fov_x_deg) * 0.5)
+    return fx, fx, 0.5 * width, 0.5 * height
+
+
+def camera_cfg0(width: int = 64, height: int = 64, distance: float = 4.0):
+    eye = np.array([distance * 0.6, -distance * 0.64, distance * 0.48])
+    eye *= distance / np.linalg.norm(eye)
+    return dict(viewmat=look_at(eye), intr=intrinsics(width, height), width=width, height=height)
+
+
+def ring_cameras(n_views: int, width: int, height: int, radius: float, seed: int):
+    """Views on a hemisphere ring band around the origin, all looking at it."""
+    rng = np.random.default_rng(seed)
+    cams = []
+    for i in range(n_views):
+        az = 2.0 * math.pi * (i + rng.uniform(-0.3, 0.3)) / n_views
+        el = math.radians(rng.uniform(5.0, 50.0))
+        eye = radius * np.array([math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), math.sin(el)])
+        cams.append(dict(viewmat=look_at(eye), intr=intrinsics(width, height),
+                         width=width, height=height))
+    return cams
+
+
+def target_image(width: int, height: int, seed: int) -> np.ndarray:
+    """(3, H, W) uniform random target image."""
+    return np.random.default_rng(seed).uniform(0.0, 1.0, size=(3, height, width))
+
+
+def _band_noise(rng, n_waves=6):
+    k = rng.normal(0.0, 3.0, size=(n_waves, 2, 3))
+    ph = rng.uniform(0, 2 * math.pi, size=(n_waves, 3))
+    amp = rng.uniform(0.2, 0.6, size=(n_waves, 3)) / n_waves ** 0.5
+
+    def f(uv):
+        out = np.zeros((uv.shape[0], 3))
+        for w in range(n_waves):
+            for ch in range(3):
+                out[:, ch] += amp[w, ch] * np.sin(uv @ k[w, :, ch] + ph[w, ch])
+        return out
+    return f
+
+
+def textured_scene(n: int, seed: int, n_surfaces: int = 20, shell_radius: float = 12.0,
+                   dtype=np.float32) -> np.ndarray:
+    """(n, 59) Gaussians on textured planes/spheres plus a background shell."""
+    rng = np.random.default_rng(seed)
+    g = np.zeros((n, NPARAM), dtype=dtype)
+    n_shell = n // 10
+    n_surf = n - n_shell
+    counts = np.full(n_surfaces, n_surf // n_surfaces)
+    counts[: n_surf - counts.sum()] += 1
+    means = np.zeros((n, 3))
+    dc = np.zeros((n, 3))
+    o = 0
+    for s in range(n_surfaces):
+        m = int(counts[s])
+        centre = rng.uniform(-1.8, 1.8, size=3)
+        uv = rng.uniform(-1.0, 1.0, size=(m, 2))
+        tex = _band_noise(rng)
+        if s % 2 == 0:  # plane patch
+            a = rng.normal(size=3); a /= np.linalg.norm(a)
+            b = np.cross(a, rng.normal(size=3)); b /= np.linalg.norm(b)
+            half = rng.uniform(0.4, 0.9)
+            means[o:o + m] = centre + half * (uv[:, :1] * a + uv[:, 1:] * b)
+        else:  # sphere
+            r = rng.uniform(0.25, 0.7)
+            th = np.arccos(uv[:, 0])
+            ph = math.pi * uv[:, 1]
+            d = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
+            means[o:o + m] = centre + r * d
+        base = rng.uniform(0.2, 0.8, size=3)
+        dc[o:o + m] = base + tex(uv * 2.0)
+        o += m
+    d = rng.normal(size=(n_shell, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    means[o:] = shell_radius * d
+    sky = _band_noise(rng)
+    dc[o:] = 0.5 + sky(d[:, :2] * 2.0)
+    g[:, 0:3] = means
+    g[:, 3:6] = rng.normal(-3.0, 0.5, size=(n, 3))
+    g[o:, 3:6] += math.log(shell_radius / 4.0)  # shell Gaussians scaled with distance
+    q = rng.normal(size=(n, 4))
+    g[:, 6:10] = q / np.linalg.norm(q, axis=1, keepdims=True)
+    g[:, 10] = rng.normal(0.0, 1.0, size=n)
+    g[:, 11:59] = rng.normal(0.0, 0.2, size=(n, 48))
+    g[:, 11:14] = (np.clip(dc, 0.0, 1.0) - 0.5) / SH_DC_NORM
+    return g
+
+
+def perturb(g: np.ndarray, seed: int, mean_sigma: float = 0.01, n_keep: int | None = None,
+            dtype=np.float32) -> np.ndarray:
+    """Initial state for optimisation: a subset of ``g`` with jittered means,
+    isotropic scales, opacity 0.1 and higher-order SH set to zero."""
+    rng = np.random.default_rng(seed)
+    idx = np.arange(g.shape[0]) if n_keep is None else np.sort(rng.choice(g.shape[0], n_keep, replace=False))
+    out = np.array(g[idx], dtype=dtype)
+    out[:, 0:3] += rng.normal(0.0, mean_sigma, size=(len(idx), 3))
+    out[:, 3:6] = out[:, 3:6].mean(axis=1, keepdims=True)
+    out[:, 6:10] = np.array([1.0, 0.0, 0.0, 0.0])
+    out[:, 10] = math.log(0.1 / 0.9)
+    out[:, 14:59] = 0.0
+    return out
