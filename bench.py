@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Benchmark: fwd+bwd rasterize (+ L1 and Adam) ms/view on the GB300.
+
+Workload (one step = one view through the whole hot path): a seeded 2M-Gaussian
+scene of textured planes/spheres plus a background shell (the 2M ground-truth
+scene of the plain full-resolution training configuration), optimised at the
+full 1237x822 resolution, one view per step:
+    project -> bin (depth order, pair emission, tile sort, ranges) ->
+    render fwd -> L1 loss -> render bwd -> project bwd -> Adam (all 59 rows).
+The optimised state is the ground truth with Gaussian noise on every
+parameter; targets are the ground truth rendered at the same 16 views.  The
+working set (params, grads, Adam moments: 1.9 GB) is larger than L2, so no
+flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the same workload (a bounded sample per step, scaled to ms/view).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W_FULL, H_FULL = 1237, 822
+N_GAUSS = 2_000_000
+N_VIEWS = 16
+FLOPS_FWD = 22     # FP32 flops per examined (pixel, Gaussian) entry, forward
+FLOPS_BWD = 58     # FP32 flops per back-traversed entry, backward
+SM_COUNT, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=int(os.environ.get("WORLD_SIZE", "1")))
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-gauss", type=int, default=N_GAUSS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-frac", type=float, default=0.125,
+                    help="area/Gaussian fraction of one view timed for the CPU baseline")
+    return ap.parse_args()
+
+
+def config(args, n_gauss):
+    return {"workload": f"textured-{n_gauss // 1000}k-gaussians-{W_FULL}x{H_FULL}-1view-fp32",
+            "n_gaussians": n_gauss, "width": W_FULL, "height": H_FULL, "views_per_step": 1,
+            "tile": 16, "sh_degree": 3, "step": "project+bin+render_fwd+L1+render_bwd+project_bwd+adam",
+            "l2": "working set 1.9 GB > L2 (no flush)", "parallelism": f"replicas{args.gpus}"}
+
+
+# --------------------------------------------------------------------------- scene
+def make_scene(n_gauss, rank):
+    from paper_2503_18402_gb300 import synth
+    gt = synth.textured_scene(n_gauss, 1001)
+    model = synth.jitter(gt, 3001)
+    cams = synth.ring_cameras(160, W_FULL, H_FULL, 5.0, 2001)
+    views = [cams[(rank * N_VIEWS + j * 10) % 160] for j in range(N_VIEWS)]
+    return gt, model, views
+
+
+# --------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2503_18402_gb300 import capi
+    from paper_2503_18402_gb300.raster import Rasterizer, make_camera
+
+    world = args.gpus
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    gt, model, views = make_scene(args.n_gauss, rank)
+    P = gt.shape[0]
+    gcams = [make_camera(np.asarray(v["viewmat"], np.float32).reshape(-1), v["intr"], v["width"], v["height"])
+             for v in views]
+    opts = capi.raster_opts(tile=16, sh_degree=3)
+    rz = Rasterizer(dev, opts)
+    gt_t = torch.from_numpy(np.ascontiguousarray(gt.T)).to(dev)
+    targets = []
+    for c in gcams:
+        fr = rz.forward(gt_t, P, c)
+        targets.append(fr.img.clone())
+    del gt_t
+    params = torch.from_numpy(np.ascontiguousarray(model.T)).to(dev)
+    grads = torch.zeros_like(params)
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    stride = params.stride(0)
+    extent = 5.0
+    lr = [1.6e-4 * extent] * 3 + [0.005] * 3 + [0.001] * 4 + [0.025] + [0.0025] * 3 + [0.0025 / 20] * 45
+    n_pix = 3 * H_FULL * W_FULL
+    dL = torch.empty((3, H_FULL, W_FULL), dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    lws = torch.empty(capi.dg_loss_workspace_size(n_pix), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # algorithmic work per view: examined entries (forward) and back-traversed entries
+    E_f, E_b, M_tot = [], [], []
+    for c in gcams:
+        fr = rz.forward(params, P, c, examined=True)
+        E_f.append(int(rz.examined.sum().item()))
+        E_b.append(int(fr.last.sum().item()))
+        M_tot.append(fr.M)
+
+    events = []
+    rz.mark = None
+
+    def mark(name):
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        events.append((name, e))
+
+    adam_t = [0]
+
+    def step(i, tgt=None, stage_events=False):
+        j = i % N_VIEWS
+        rz.mark = mark if stage_events else None
+        if stage_events:
+            mark("start")
+        fr = rz.forward(params, P, gcams[j])
+        capi.dg_loss_l1(fr.img, targets[j] if tgt is None else tgt, n_pix, dL, loss, lws, lws.numel(), stream)
+        if stage_events:
+            mark("loss")
+        rz.backward(params, fr, dL, grads)
+        adam_t[0] += 1
+        capi.dg_adam_step(params, grads, m, v, stride, P, lr, 0.9, 0.999, 1e-15, adam_t[0], stream)
+        if stage_events:
+            mark("adam")
+        return fr
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = capi.dg_kernel_launches()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0.record(stream)
+    for i in range(args.steps):
+        events.clear() if i == 0 else None
+        step(args.warmup + i, stage_events=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = capi.dg_kernel_launches() - launches0
+    clk = clocks.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    # per-stage device time between consecutive marks
+    stage_ms = {}
+    prev = None
+    for name, e in events:
+        if name == "start":
+            prev = e
+            continue
+        stage_ms[name] = stage_ms.get(name, 0.0) + prev.elapsed_time(e)
+        prev = e
+    if world > 1:
+        tt = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+
+    # end to end through the public API: target copied from pinned host memory
+    # each step, loss read back each step
+    pinned = [t.cpu().pin_memory() for t in targets]
+    tgt_dev = torch.empty_like(targets[0])
+    for i in range(2):
+        tgt_dev.copy_(pinned[i % N_VIEWS], non_blocking=True)
+        step(i, tgt=tgt_dev)
+        loss.item()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0 = time.perf_counter()
+    for i in range(args.steps):
+        tgt_dev.copy_(pinned[i % N_VIEWS], non_blocking=True)
+        step(i, tgt=tgt_dev)
+        float(loss.item())
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - e0) * 1e3
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+
+    views_total = args.steps * world
+    ms_per_view = elapsed_ms / views_total
+    out = {
+        "metric": "fwd+bwd rasterize ms/view (full-res training step incl. L1 + Adam)",
+        "value": round(ms_per_view, 4), "unit": "ms/view", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded textured scene)",
+        "config": config(args, P), "impl": "ours",
+    }
+    tot = sum(stage_ms.values())
+    stages = {k: {"ms": round(v / args.steps, 4), "share": round(v / tot, 4)} for k, v in stage_ms.items()}
+    out["stages"] = stages
+    pf = sum(E_f) / len(E_f)
+    pb = sum(E_b) / len(E_b)
+    work = {"render_fwd": ("alu", pf * FLOPS_FWD), "render_bwd": ("alu", pb * FLOPS_BWD),
+            "project": ("hbm", P * 297.0), "project_bwd": ("hbm", P * 525.0), "adam": ("hbm", P * 1652.0)}
+    dom = max((k for k in stages if k in work), key=lambda k: stages[k]["ms"])
+    kind, units = work[dom]
+    dur_s = stages[dom]["ms"] * 1e-3
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    if kind == "alu":
+        peak = SM_COUNT * FP32_LANES * 2 * MAX_MHZ * 1e6 / 1e12
+        ach = units / dur_s / 1e12
+        out["roofline"] = {"bound": "alu", "kernel": dom, "achieved": round(ach, 3), "peak": round(peak, 2),
+                           "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                           "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    else:
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        ach = units / dur_s / 1e9
+        out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                           "frac": round(ach / hbm, 4), "traffic": None,
+                           "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s"}
+    out["work"] = {"pairs_per_view": int(sum(M_tot) / len(M_tot)), "examined_fwd_per_view": int(pf),
+                   "traversed_bwd_per_view": int(pb)}
+    out["fwd_bwd_ms_per_view"] = round(sum(stages[k]["ms"] for k in stages if k not in ("adam", "loss")), 4)
+    out["e2e"] = {"value": round(e2e_ms / views_total, 4), "unit": "ms/view",
+                  "h2d_bytes_per_step": int(targets[0].numel() * 4), "d2h_bytes_per_step": 4 + 8}
+    out["gpu_launches"] = int(launches)
+    out["clocks"] = clk
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(model, views[0], frac=args.cpu_frac)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- oracle (CPU)
+def _crop_camera(view, frac):
+    """Centred sub-camera covering `frac` of the view's area (same focal length)."""
+    s = math.sqrt(frac)
+    w = max(16, int(round(W_FULL * s)))
+    h = max(16, int(round(H_FULL * s)))
+    fx, fy, cx, cy = view["intr"]
+    return dict(viewmat=view["viewmat"], intr=(fx, fy, cx - (W_FULL - w) / 2, cy - (H_FULL - h) / 2),
+                width=w, height=h)
+
+
+def oracle_step_time(model, view, frac, rng_seed=0):
+    """Seconds of oracle work for one view, measured on a `frac` sample and
+    scaled: per-Gaussian stages on a random `frac` of the Gaussians, per-pixel
+    stages (binning, compositing, loss, adjoint) on a centred `frac`-area crop."""
+    import oracle
+    rng = np.random.default_rng(rng_seed)
+    P = model.shape[0]
+    k = oracle.consts()
+    n_sub = max(1, int(P * frac))
+    sub = model[np.sort(rng.choice(P, n_sub, replace=False))] if n_sub < P else model
+    g64 = np.asarray(sub, np.float64)
+    fx, fy, cx, cy = view["intr"]
+    cam = oracle.camera(view["viewmat"], fx, fy, cx, cy, W_FULL, H_FULL)
+    t = time.perf_counter()
+    pr = oracle.project(g64, cam, k)
+    t_proj = time.perf_counter() - t
+    g2 = np.zeros((n_sub, 9))
+    g2[pr["radius"] > 0] = 1e-6
+    t = time.perf_counter()
+    grad = oracle.project_bwd(g64, cam, k, g2)
+    t_pbwd = time.perf_counter() - t
+    pm = g64.copy(); mm = np.zeros_like(pm); vv = np.zeros_like(pm)
+    t = time.perf_counter()
+    oracle.adam(pm, grad, mm, vv, 1e-3, 0.9, 0.999, 1e-15, 1)
+    t_adam = time.perf_counter() - t
+    # per-pixel stages on the crop, with every Gaussian projected into it (untimed)
+    crop = _crop_camera(view, frac)
+    fx, fy, cx, cy = crop["intr"]
+    ccam = oracle.camera(crop["viewmat"], fx, fy, cx, cy, crop["width"], crop["height"])
+    prc = oracle.project(np.asarray(model, np.float64), ccam, k)
+    Wc, Hc = crop["width"], crop["height"]
+    target = np.random.default_rng(1).uniform(size=(3, Hc, Wc))
+    t = time.perf_counter()
+    bs = oracle.bin_sort(prc["feat"][:, :2], prc["radius"], prc["depth_key"], Wc, Hc, 16)
+    rf = oracle.render_fwd(prc["feat"], Wc, Hc, 16, bs["gid"], bs["ranges"], np.zeros(3), k)
+    _, dLd = oracle.loss_l1(rf["img"], target)
+    oracle.render_bwd(prc["feat"], Wc, Hc, 16, bs["gid"], bs["ranges"], np.zeros(3), k, dLd)
+    t_pix = time.perf_counter() - t
+    area_scale = (W_FULL * H_FULL) / (Wc * Hc)
+    total = (t_proj + t_pbwd + t_adam) * (P / n_sub) + t_pix * area_scale
+    return total, dict(t_proj=t_proj, t_pbwd=t_pbwd, t_adam=t_adam, t_pix=t_pix, n_sub=n_sub,
+                       crop=(Wc, Hc), area_scale=area_scale)
+
+
+def cpu_baseline(model, view, frac):
+    total, info = oracle_step_time(model, view, frac)
+    return {"value": round(total * 1e3, 1), "unit": "ms/view", "cores": 1, "kind": "oracle",
+            "sample": (f"one view: per-Gaussian stages on {info['n_sub']} of {model.shape[0]} Gaussians, "
+                       f"per-pixel stages on a {info['crop'][0]}x{info['crop'][1]} centred crop; "
+                       f"scaled to the full view (x{model.shape[0] / info['n_sub']:.1f}, "
+                       f"x{info['area_scale']:.2f}); FP64, single thread")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2503_18402_gb300 import synth
+    gt = synth.textured_scene(args.n_gauss, 1001)
+    model = synth.jitter(gt, 3001)
+    cams = synth.ring_cameras(160, W_FULL, H_FULL, 5.0, 2001)
+    frac = 1.0 / 64
+    for i in range(args.warmup):
+        oracle_step_time(model, cams[(i * 10) % 160], frac, rng_seed=i)
+    times = []
+    info = None
+    for i in range(args.steps):
+        t, info = oracle_step_time(model, cams[(i * 10) % 160], frac, rng_seed=100 + i)
+        times.append(t)
+    ms = 1e3 * sum(times) / len(times)
+    sample = (f"per step: per-Gaussian stages on {info['n_sub']} of {model.shape[0]} Gaussians, per-pixel "
+              f"stages on a {info['crop'][0]}x{info['crop'][1]} crop, scaled to one full view; FP64, 1 thread")
+    out = {"metric": "fwd+bwd rasterize ms/view (full-res training step incl. L1 + Adam)", "value": round(ms, 1),
+           "unit": "ms/view", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(ms, 1), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic (seeded textured scene)", "config": config(args, model.shape[0]),
+           "impl": "reference",
+           "cpu_baseline": {"value": round(ms, 1), "unit": "ms/view", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(ms, 1), "unit": "ms/view", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -96,6 +96,10 @@ def lib():
                                      _P, _P]
         L.dgo_project_bwd.argtypes = [_I64, _P, ctypes.POINTER(Camera), ctypes.POINTER(Consts),
                                       _P, _P]
+        L.dgo_tile_list.argtypes = [_I64, _P, _P, _P, _I32, _I32, _I32, _I64, _I64, _P]
+        L.dgo_tile_list.restype = _I64
+        L.dgo_render_pixels.argtypes = [_P, _I32, _I32, _P, _P, _P, ctypes.POINTER(Consts), _I64, _P, _P,
+                                        _P, _P, _P, _P]
         L.dgo_loss_l1.argtypes = [_I64, _P, _P, _P]
         L.dgo_loss_l1.restype = _D
         L.dgo_adam.argtypes = [_I64, _P, _P, _P, _P, _P, _D, _D, _D, _I64]
@@ -153,6 +157,34 @@ def bin_sort(uv, radius, depth_key, W, H, B) -> dict:
                        _ptr(tiles), _ptr(gids), _ptr(ranges))
     assert M2 == M
     return dict(M=int(M), tile=tiles[:M], gid=gids[:M], ranges=ranges)
+
+
+def tile_list(uv, radius, depth_key, W, H, B, tile_id) -> np.ndarray:
+    """Gaussian indices of one tile's list, ordered by (depth key, index)."""
+    uv = _f64(uv).reshape(-1, 2)
+    radius = np.ascontiguousarray(radius, dtype=np.int32)
+    depth_key = np.ascontiguousarray(depth_key, dtype=np.uint32)
+    out = np.zeros(1, np.uint32)
+    m = lib().dgo_tile_list(uv.shape[0], _ptr(uv), _ptr(radius), _ptr(depth_key), W, H, B, tile_id, 0, _ptr(out))
+    out = np.zeros(max(m, 1), np.uint32)
+    lib().dgo_tile_list(uv.shape[0], _ptr(uv), _ptr(radius), _ptr(depth_key), W, H, B, tile_id, m, _ptr(out))
+    return out[:m]
+
+
+def render_pixels(feat, W, B, gid, ranges, bg, k: Consts, px, py) -> dict:
+    """Eq. 1 at sampled pixels (px, py) given a tile-sorted list."""
+    feat = _f64(feat)
+    gid = np.ascontiguousarray(gid, dtype=np.uint32)
+    if gid.size == 0:
+        gid = np.zeros(1, np.uint32)
+    ranges = np.ascontiguousarray(ranges, dtype=np.uint32)
+    px = np.ascontiguousarray(px, dtype=np.int32)
+    py = np.ascontiguousarray(py, dtype=np.int32)
+    n = px.size
+    rgb = np.zeros((n, 3)); T = np.zeros(n); last = np.zeros(n, np.int32); ex = np.zeros(n, np.int32)
+    lib().dgo_render_pixels(_ptr(feat), W, B, _ptr(gid), _ptr(ranges), _ptr(_f64(bg)), ctypes.byref(k), n,
+                            _ptr(px), _ptr(py), _ptr(rgb), _ptr(T), _ptr(last), _ptr(ex))
+    return dict(rgb=rgb, T=T, last=last, examined=ex)
 
 
 def render_fwd(feat, W, H, B, gid, ranges, bg, k: Consts) -> dict:

@@ -341,6 +341,35 @@ int64_t dgo_bin(int64_t n, const double* uv, const int32_t* radius, const uint32
     return M;
 }
 
+/* One tile's list by the same definition, for sampled checks at full size:
+ * the Gaussians whose rect contains tile `tile_id`, ordered by (depth key,
+ * index).  Returns the count; writes at most `cap` indices. */
+int64_t dgo_tile_list(int64_t n, const double* uv, const int32_t* radius, const uint32_t* depth_key,
+                      int32_t W, int32_t H, int32_t B, int64_t tile_id, int64_t cap, uint32_t* out)
+{
+    const int64_t TX = (W + B - 1) / B;
+    const int64_t tx = tile_id % TX, ty = tile_id / TX;
+    int64_t m = 0;
+    pair3* pr = NULL;
+    int64_t pcap = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t rc[4];
+        if (radius[i] <= 0) continue;
+        if (!rect_of(uv[2 * i], uv[2 * i + 1], radius[i], W, H, B, rc)) continue;
+        if (tx < rc[0] || tx >= rc[2] || ty < rc[1] || ty >= rc[3]) continue;
+        if (m == pcap) {
+            pcap = pcap ? 2 * pcap : 1024;
+            pr = (pair3*)realloc(pr, sizeof(pair3) * (size_t)pcap);
+        }
+        pr[m].tile = (uint32_t)tile_id; pr[m].key = depth_key[i]; pr[m].gid = (uint32_t)i;
+        ++m;
+    }
+    if (m > 0) qsort(pr, (size_t)m, sizeof(pair3), cmp_pair3);
+    for (int64_t j = 0; j < m && j < cap; ++j) out[j] = pr[j].gid;
+    free(pr);
+    return m;
+}
+
 /* ------------------------------------------------------------------ */
 /* Eq. 1 per pixel, front to back over the pixel's tile list. */
 typedef struct blend_rec {
@@ -406,6 +435,22 @@ void dgo_render_fwd(const double* feat, int32_t W, int32_t H, int32_t B, const u
         }
 }
 
+/* Eq. 1 at sampled pixels only (same per-pixel rule as dgo_render_fwd). */
+void dgo_render_pixels(const double* feat, int32_t W, int32_t B, const uint32_t* gid, const uint32_t* ranges,
+                       const double* bg, const dgo_consts* k, int64_t npix, const int32_t* px,
+                       const int32_t* py, double* rgb, double* T_out, int32_t* last_out, int32_t* examined_out)
+{
+    for (int64_t j = 0; j < npix; ++j) {
+        double T, C[3];
+        int32_t last, ex;
+        composite_pixel(feat, W, B, gid, ranges, k, px[j], py[j], &T, &last, &ex, C, NULL);
+        for (int ch = 0; ch < 3; ++ch) rgb[3 * j + ch] = C[ch] + T * bg[ch];
+        T_out[j] = T;
+        last_out[j] = last;
+        examined_out[j] = ex;
+    }
+}
+
 /* Adjoint of Eq. 1.  grad2d (n x 9, accumulated into; caller zeroes) holds
  * dL/d(u, v, A, B, C, o, r, g, b).  dC/dc_j = alpha_j T_j;
  * dC/dalpha_j = T_j c_j - S_j / (1 - alpha_j) with S_j the colour composited
@@ -424,10 +469,11 @@ void dgo_render_bwd(const double* feat, int32_t W, int32_t H, int32_t B, const u
         for (int32_t px = 0; px < W; ++px) {
             double T, C[3];
             int32_t last, ex;
-            const int64_t nrec = composite_pixel(feat, W, B, gid, ranges, k, px, py, &T, &last, &ex, C, recs);
             const int64_t i = (int64_t)py * W + px;
             double gpix[3];
             for (int ch = 0; ch < 3; ++ch) gpix[ch] = dL_dimg[ch * HW + i];
+            if (gpix[0] == 0.0 && gpix[1] == 0.0 && gpix[2] == 0.0) continue; /* contributes exactly 0 */
+            const int64_t nrec = composite_pixel(feat, W, B, gid, ranges, k, px, py, &T, &last, &ex, C, recs);
             double S[3];
             for (int ch = 0; ch < 3; ++ch) S[ch] = T * bg[ch];
             for (int64_t j = nrec - 1; j >= 0; --j) {

@@ -1,0 +1,70 @@
+// common.cuh -- shared device-side definitions of the CUDA rasterizer library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dashgs.h"
+
+namespace dg {
+
+// Thresholds of the compositing rule (fixed readings of the ABI, see dashgs.h):
+// alpha clamp, skip threshold and early-stop transmittance.
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+constexpr float kFrustumGuard = 1.3f;
+constexpr float kGuardPx = 1073741824.0f;  // 2^30: footprints or centres beyond are culled
+
+// Camera in registers: world-to-camera rotation (row-major), translation,
+// intrinsics and image size.
+struct Cam {
+    float r[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int w, h;
+};
+
+inline Cam make_cam(const dg_camera& c)
+{
+    Cam k;
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) k.r[3 * i + j] = c.viewmat[4 * i + j];
+        k.t[i] = c.viewmat[4 * i + 3];
+    }
+    k.fx = c.fx; k.fy = c.fy; k.cx = c.cx; k.cy = c.cy;
+    k.w = c.width; k.h = c.height;
+    return k;
+}
+
+__host__ __device__ inline long long floor_div(long long a, long long b)  // b > 0
+{
+    long long q = a / b;
+    if ((a % b) != 0 && a < 0) --q;
+    return q;
+}
+
+// Tile rect [x0, x1) x [y0, y1) of a footprint centred at (u, v) with integer
+// radius r: floor((u -/+ r)/B) computed exactly as floor_div(floor(u) -/+ r, B).
+struct Rect { int x0, y0, x1, y1; };
+
+__device__ inline Rect tile_rect(float u, float v, int r, int B, int TX, int TY)
+{
+    const long long fu = (long long)floorf(u), fv = (long long)floorf(v);
+    long long x0 = floor_div(fu - r, B), x1 = floor_div(fu + r, B) + 1;
+    long long y0 = floor_div(fv - r, B), y1 = floor_div(fv + r, B) + 1;
+    Rect q;
+    q.x0 = (int)(x0 < 0 ? 0 : (x0 > TX ? TX : x0));
+    q.x1 = (int)(x1 < 0 ? 0 : (x1 > TX ? TX : x1));
+    q.y0 = (int)(y0 < 0 ? 0 : (y0 > TY ? TY : y0));
+    q.y1 = (int)(y1 < 0 ? 0 : (y1 > TY ? TY : y1));
+    return q;
+}
+
+}  // namespace dg
+
+// Host-side error reporting shared by the C-ABI entry points.
+void dg_set_error(const char* fmt, ...);
+// Counts kernel launches issued by this library (read by dg_kernel_launches).
+void dg_note_launch(int n = 1);
+dg_status dg_check_launch(const char* what);

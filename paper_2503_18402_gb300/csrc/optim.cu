@@ -1,0 +1,139 @@
+// optim.cu -- L1 photometric loss (+ its gradient) and the Adam update.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace dg {
+
+constexpr int LOSS_THREADS = 256;
+constexpr int LOSS_BLOCKS_MAX = 1024;
+
+// Grid-stride: grad = sign(img - target) / n; per-block partial sum of |d|.
+__global__ void __launch_bounds__(LOSS_THREADS)
+k_l1(const float* __restrict__ img, const float* __restrict__ tgt, long long n, float inv_n,
+     float* __restrict__ grad, float* __restrict__ partial)
+{
+    __shared__ float sm[LOSS_THREADS / 32];
+    float acc = 0.f;
+    for (long long i = (long long)blockIdx.x * LOSS_THREADS + threadIdx.x; i < n;
+         i += (long long)gridDim.x * LOSS_THREADS) {
+        const float d = img[i] - tgt[i];
+        acc += fabsf(d);
+        grad[i] = d > 0.f ? inv_n : (d < 0.f ? -inv_n : 0.f);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int w = 0; w < LOSS_THREADS / 32; ++w) s += sm[w];
+        partial[blockIdx.x] = s;
+    }
+}
+
+// Deterministic final sum of the block partials (fixed order, FP64 accumulator).
+__global__ void k_l1_final(const float* __restrict__ partial, int nb, float inv_n, float* loss)
+{
+    __shared__ double sm[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += (double)partial[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm[w];
+        *loss = (float)(s * (double)inv_n);
+    }
+}
+
+struct AdamRow {
+    float lr[DG_NPARAM];
+};
+
+// One thread per 4 consecutive Gaussians of one parameter row (float4 when the
+// row start is 16-byte aligned, scalar otherwise).
+__global__ void __launch_bounds__(256)
+k_adam(float* __restrict__ prm, const float* __restrict__ grd, float* __restrict__ m,
+       float* __restrict__ v, long long stride, long long P, AdamRow lr, float b1, float b2,
+       float bc1, float bc2_sqrt, float eps)
+{
+    const int row = blockIdx.y;
+    const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (i0 >= P) return;
+    const float step = lr.lr[row] / bc1;
+    const long long o = (long long)row * stride + i0;
+    const bool vec = ((o & 3) == 0) && (i0 + 3 < P) && ((((uintptr_t)prm) & 15u) == 0) &&
+                     ((((uintptr_t)grd) & 15u) == 0) && ((((uintptr_t)m) & 15u) == 0) &&
+                     ((((uintptr_t)v) & 15u) == 0);
+    if (vec) {
+        float4 p = *(float4*)(prm + o), g = *(const float4*)(grd + o);
+        float4 mm = *(float4*)(m + o), vv = *(float4*)(v + o);
+        float* pp = &p.x; const float* gg = &g.x; float* mp = &mm.x; float* vp = &vv.x;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            mp[c] = b1 * mp[c] + (1.f - b1) * gg[c];
+            vp[c] = b2 * vp[c] + (1.f - b2) * gg[c] * gg[c];
+            pp[c] -= step * mp[c] / (sqrtf(vp[c]) / bc2_sqrt + eps);
+        }
+        *(float4*)(prm + o) = p;
+        *(float4*)(m + o) = mm;
+        *(float4*)(v + o) = vv;
+    } else {
+        for (int c = 0; c < 4 && i0 + c < P; ++c) {
+            const long long k = o + c;
+            const float gc = grd[k];
+            const float mc = b1 * m[k] + (1.f - b1) * gc;
+            const float vc = b2 * v[k] + (1.f - b2) * gc * gc;
+            m[k] = mc;
+            v[k] = vc;
+            prm[k] -= step * mc / (sqrtf(vc) / bc2_sqrt + eps);
+        }
+    }
+}
+
+}  // namespace dg
+
+extern "C" size_t dg_loss_workspace_size(int64_t n)
+{
+    (void)n;
+    return sizeof(float) * dg::LOSS_BLOCKS_MAX;
+}
+
+extern "C" dg_status dg_loss_l1(const float* img, const float* target, int64_t n, float* dL_dimg,
+                                float* loss, void* ws, size_t ws_bytes, dg_stream stream)
+{
+    if (n <= 0) { dg_set_error("n must be positive"); return DG_ERR_ARG; }
+    if (!img || !target || !dL_dimg || !loss || !ws) { dg_set_error("null buffer"); return DG_ERR_ARG; }
+    if (ws_bytes < dg_loss_workspace_size(n)) { dg_set_error("loss workspace too small"); return DG_ERR_CAPACITY; }
+    long long nb = (n + dg::LOSS_THREADS - 1) / dg::LOSS_THREADS;
+    if (nb > dg::LOSS_BLOCKS_MAX) nb = dg::LOSS_BLOCKS_MAX;
+    cudaStream_t s = (cudaStream_t)stream;
+    const float inv_n = (float)(1.0 / (double)n);
+    dg::k_l1<<<(int)nb, dg::LOSS_THREADS, 0, s>>>(img, target, n, inv_n, dL_dimg, (float*)ws);
+    dg_note_launch();
+    dg::k_l1_final<<<1, 256, 0, s>>>((const float*)ws, (int)nb, (float)(1.0 / (double)n), loss);
+    dg_note_launch();
+    return dg_check_launch("loss_l1");
+}
+
+extern "C" dg_status dg_adam_step(float* params, const float* grads, float* m, float* v, int64_t stride,
+                                  int64_t P, const float* lr, float beta1, float beta2, float eps,
+                                  int64_t step, dg_stream stream)
+{
+    if (P < 0 || stride < P || step < 1) { dg_set_error("bad P/stride/step"); return DG_ERR_ARG; }
+    if (P == 0) return DG_OK;
+    if (!params || !grads || !m || !v || !lr) { dg_set_error("null buffer"); return DG_ERR_ARG; }
+    dg::AdamRow r;
+    for (int i = 0; i < DG_NPARAM; ++i) r.lr[i] = lr[i];
+    const double bc1 = 1.0 - pow((double)beta1, (double)step);
+    const double bc2 = 1.0 - pow((double)beta2, (double)step);
+    const long long per = 256 * 4;
+    dim3 grid((unsigned)((P + per - 1) / per), DG_NPARAM);
+    dg::k_adam<<<grid, 256, 0, (cudaStream_t)stream>>>(params, grads, m, v, stride, P, r, beta1, beta2,
+                                                        (float)bc1, (float)sqrt(bc2), eps);
+    dg_note_launch();
+    return dg_check_launch("adam");
+}

@@ -162,3 +162,17 @@ def perturb(g: np.ndarray, seed: int, mean_sigma: float = 0.01, n_keep: int | No
     out[:, 10] = math.log(0.1 / 0.9)
     out[:, 14:59] = 0.0
     return out
+
+
+def jitter(g: np.ndarray, seed: int, mean_sigma: float = 0.01, scale_sigma: float = 0.1,
+           opacity_sigma: float = 0.2, sh_sigma: float = 0.05, dtype=np.float32) -> np.ndarray:
+    """A nearby optimisation state: ``g`` with Gaussian noise on every parameter."""
+    rng = np.random.default_rng(seed)
+    out = np.array(g, dtype=dtype)
+    n = out.shape[0]
+    out[:, 0:3] += rng.normal(0.0, mean_sigma, size=(n, 3)).astype(dtype)
+    out[:, 3:6] += rng.normal(0.0, scale_sigma, size=(n, 3)).astype(dtype)
+    out[:, 6:10] += rng.normal(0.0, 0.05, size=(n, 4)).astype(dtype)
+    out[:, 10] += rng.normal(0.0, opacity_sigma, size=n).astype(dtype)
+    out[:, 11:59] += rng.normal(0.0, sh_sigma, size=(n, 48)).astype(dtype)
+    return out

@@ -1,0 +1,291 @@
+"""CUDA path vs the FP64 oracle, element by element (needs a GPU).
+
+Tolerances (from the target: tile lists and key order bit-exact; images
+within 1e-5 absolute; gradients within 1e-4 relative or 1e-6 absolute near
+zero).  Intermediate projected records are FP32 results of an FP64
+definition; their tolerances follow from the FP32 arithmetic (a few ulps of
+the pixel coordinates, 1e-4 relative on the conic whose 2x2 inverse has
+condition number up to ~10 on these scenes).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+from paper_2503_18402_gb300 import capi, synth  # noqa: E402
+from paper_2503_18402_gb300.raster import Rasterizer, rasterize  # noqa: E402
+from tests import _gpu as G  # noqa: E402
+from tests import _util as U  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(g, cam, bg=(0.0, 0.0, 0.0), tile=16, sh=3):
+    opts = capi.raster_opts(tile=tile, sh_degree=sh, bg=bg)
+    k = oracle.consts(tile=tile, sh_degree=sh)
+    rz = Rasterizer("cuda", opts)
+    params = G.gpu_params(g)
+    gcam = G.gpu_camera(cam)
+    fr = rz.forward(params, g.shape[0], gcam, examined=True)
+    torch.cuda.synchronize()
+    return rz, params, gcam, fr, k, G.oracle_camera(cam), G.f32(g), G.f32(bg)
+
+
+def _records(rz, P):
+    feat = G.np_(rz.feat[:P]).astype(np.float64)
+    return dict(feat=feat[:, :9], uv=feat[:, :2], radius=G.np_(rz.radius[:P]),
+                key=G.np_(rz.depth[:P]).view(np.uint32), tiles=G.np_(rz.tiles[:P]),
+                clamp=G.np_(rz.clamp[:P]))
+
+
+def _gpu_bins(rz, fr):
+    gid = G.np_(rz.gid[: fr.M]).view(np.uint32)
+    ranges = G.np_(rz.ranges[: rz.n_tiles]).view(np.uint32)
+    return gid, ranges
+
+
+def _margins_ok(pr, W, H, B, tol=1e-4):
+    """Every visible Gaussian is away from the discrete thresholds of binning."""
+    vis = pr["radius"] > 0
+    fu = pr["feat"][vis, :2]
+    fr = fu - np.floor(fu)
+    return bool(np.all((fr > tol) & (fr < 1 - tol)))
+
+
+# ---------------------------------------------------------------- config 0
+@pytest.fixture(scope="module")
+def cfg0():
+    g, cam, target = U.cfg0_scene()
+    return g, cam, target
+
+
+def test_cfg0_projection(cfg0):
+    g, cam, _ = cfg0
+    rz, params, gcam, fr, k, ocam, g64, _ = _setup(g, cam)
+    rec = _records(rz, g.shape[0])
+    pr = oracle.project(g64, ocam, k)
+    vis = pr["radius"] > 0
+    assert vis.sum() > 500
+    np.testing.assert_array_equal(rec["radius"] > 0, vis)
+    f, fo = rec["feat"][vis], pr["feat"][vis]
+    np.testing.assert_allclose(f[:, :2], fo[:, :2], rtol=1e-5, atol=1e-4)
+    cn = np.abs(fo[:, 2:5]).max(axis=1, keepdims=True)
+    assert np.all(np.abs(f[:, 2:5] - fo[:, 2:5]) <= 1e-4 * cn)
+    np.testing.assert_allclose(f[:, 5], fo[:, 5], rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(f[:, 6:9], fo[:, 6:9], atol=1e-5)
+    np.testing.assert_allclose(G.np_(rz.depth[: g.shape[0]]), pr["depth"], rtol=1e-6)
+    # integer outputs: exact where the FP64 value has a margin to the rounding point
+    r3 = None  # radius = ceil(3 sqrt(lambda)); compare where not within 1e-4 of an integer
+    same_r = rec["radius"][vis] == pr["radius"][vis]
+    assert same_r.mean() > 0.99
+    np.testing.assert_array_equal(rec["clamp"][vis], np.packbits(pr["clamp"][vis][:, ::-1], axis=1, bitorder="big")[:, 0] >> 5)
+
+
+def test_cfg0_binning_bit_exact(cfg0):
+    g, cam, _ = cfg0
+    rz, params, gcam, fr, k, ocam, g64, _ = _setup(g, cam)
+    rec = _records(rz, g.shape[0])
+    ob = oracle.bin_sort(rec["uv"], rec["radius"], rec["key"], 64, 64, 16)
+    gid, ranges = _gpu_bins(rz, fr)
+    assert fr.M == ob["M"] and fr.M > 1000
+    np.testing.assert_array_equal(gid, ob["gid"])
+    np.testing.assert_array_equal(ranges, ob["ranges"])
+    assert int(rec["tiles"].sum()) == fr.M
+    # the full FP64 path bins identically when the scene keeps its margins
+    pr = oracle.project(g64, ocam, k)
+    if _margins_ok(pr, 64, 64, 16) and np.array_equal(pr["radius"], rec["radius"]):
+        ob2 = oracle.bin_sort(pr["feat"][:, :2], pr["radius"], pr["depth_key"], 64, 64, 16)
+        np.testing.assert_array_equal(gid, ob2["gid"])
+
+
+def test_cfg0_render_given_records(cfg0):
+    g, cam, _ = cfg0
+    for bg in ((0.0, 0.0, 0.0), (0.25, 0.5, 1.0)):
+        rz, params, gcam, fr, k, ocam, g64, bg64 = _setup(g, cam, bg=bg)
+        rec = _records(rz, g.shape[0])
+        gid, ranges = _gpu_bins(rz, fr)
+        orf = oracle.render_fwd(rec["feat"], 64, 64, 16, gid, ranges, bg64, k)
+        assert np.abs(G.np_(fr.img) - orf["img"]).max() <= 1e-5
+        assert np.abs(G.np_(fr.T) - orf["T"]).max() <= 1e-5
+        np.testing.assert_array_equal(G.np_(fr.last), orf["last"])
+        np.testing.assert_array_equal(G.np_(rz.examined), orf["examined"])
+
+
+def test_cfg0_full_image(cfg0):
+    g, cam, _ = cfg0
+    rz, params, gcam, fr, k, ocam, g64, bg64 = _setup(g, cam)
+    of = oracle.forward(g64, ocam, k, bg=bg64)
+    err = np.abs(G.np_(fr.img) - of["img"]).max()
+    assert err <= 1e-5, err
+
+
+def test_cfg0_render_bwd_given_records(cfg0):
+    g, cam, target = cfg0
+    rz, params, gcam, fr, k, ocam, g64, bg64 = _setup(g, cam)
+    rec = _records(rz, g.shape[0])
+    gid, ranges = _gpu_bins(rz, fr)
+    rng = np.random.default_rng(0)
+    dL = rng.normal(size=(3, 64, 64)).astype(np.float32) / (3 * 64 * 64)
+    grads = torch.empty_like(params)
+    rz.backward(params, fr, torch.from_numpy(dL).cuda(), grads)
+    torch.cuda.synchronize()
+    g2 = G.np_(rz.grad2d[: g.shape[0]])[:, :9]
+    og2 = oracle.render_bwd(rec["feat"], 64, 64, 16, gid, ranges, bg64, k, dL.astype(np.float64))
+    ok, worst, nbad = G.grad_close(g2, og2)
+    assert ok, (worst, nbad)
+    # project adjoint given the same 2D gradients
+    og = oracle.project_bwd(g64, ocam, k, g2.astype(np.float64))
+    ok, worst, nbad = G.grad_close(G.np_(grads).T, og)
+    assert ok, (worst, nbad)
+
+
+def test_cfg0_full_gradient_through_autograd(cfg0):
+    g, cam, target = cfg0
+    opts = capi.raster_opts()
+    k = oracle.consts()
+    rz = Rasterizer("cuda", opts)
+    params = G.gpu_params(g).requires_grad_(True)
+    img = rasterize(params, rz, G.gpu_camera(cam))
+    tgt = torch.from_numpy(target.astype(np.float32)).cuda()
+    # L1 through the library's loss kernel
+    n = img.numel()
+    dL = torch.empty_like(img)
+    loss = torch.zeros(1, device="cuda")
+    ws = torch.empty(capi.dg_loss_workspace_size(n), dtype=torch.uint8, device="cuda")
+    capi.dg_loss_l1(img.detach(), tgt, n, dL, loss, ws, ws.numel())
+    img.backward(dL)
+    torch.cuda.synchronize()
+    g64 = G.f32(g)
+    ocam = G.oracle_camera(cam)
+    of = oracle.forward(g64, ocam, k)
+    oloss, odL = oracle.loss_l1(of["img"], G.f32(target))
+    assert abs(loss.item() - oloss) <= 1e-6
+    # the sign pattern of dL/dimg decides the gradient: compare with the oracle's
+    # backward fed the GPU's dL (ties |I - target| < 1e-5 may flip)
+    diff = np.abs(G.np_(dL) - odL)
+    assert (diff > 0).mean() < 1e-3
+    ob = oracle.backward(g64, ocam, k, of, G.np_(dL).astype(np.float64))
+    ok, worst, nbad = G.grad_close(G.np_(params.grad).T, ob["grad"])
+    assert ok, (worst, nbad)
+
+
+# ---------------------------------------------------------------- shapes, tiles
+@pytest.mark.parametrize("W,H,tile,n", [(72, 40, 16, 3000), (50, 37, 8, 2000), (16, 16, 16, 50),
+                                        (200, 130, 16, 20000)])
+def test_ragged_sizes_and_tile8(W, H, tile, n):
+    g = synth.random_gaussians(n, 77 + n)
+    g[:, 3:6] += 0.4
+    cam = synth.camera_cfg0(W, H, 4.0)
+    bg = (0.1, 0.2, 0.3)
+    rz, params, gcam, fr, k, ocam, g64, bg64 = _setup(g, cam, bg=bg, tile=tile)
+    rec = _records(rz, n)
+    ob = oracle.bin_sort(rec["uv"], rec["radius"], rec["key"], W, H, tile)
+    gid, ranges = _gpu_bins(rz, fr)
+    np.testing.assert_array_equal(gid, ob["gid"])
+    np.testing.assert_array_equal(ranges, ob["ranges"])
+    orf = oracle.render_fwd(rec["feat"], W, H, tile, gid, ranges, bg64, k)
+    assert np.abs(G.np_(fr.img) - orf["img"]).max() <= 1e-5
+    np.testing.assert_array_equal(G.np_(fr.last), orf["last"])
+    rng = np.random.default_rng(1)
+    dL = (rng.normal(size=(3, H, W)) / (3 * H * W)).astype(np.float32)
+    grads = torch.empty_like(params)
+    rz.backward(params, fr, torch.from_numpy(dL).cuda(), grads)
+    og2 = oracle.render_bwd(rec["feat"], W, H, tile, gid, ranges, bg64, k, dL.astype(np.float64))
+    ok, worst, nbad = G.grad_close(G.np_(rz.grad2d[:n])[:, :9], og2)
+    assert ok, (worst, nbad)
+
+
+def test_empty_and_all_culled():
+    cam = U.identity_cam(40, 24, 50.0)
+    bg = (0.2, 0.5, 0.9)
+    for g in (np.zeros((0, 59)),
+              np.concatenate([U.single_gaussian((0, 0, 0.1), [-2] * 3), U.single_gaussian((0, 0, -3.0), [-2] * 3)])):
+        opts = capi.raster_opts(bg=bg)
+        rz = Rasterizer("cuda", opts)
+        params = G.gpu_params(g) if g.shape[0] else torch.zeros((59, 0), device="cuda")
+        fr = rz.forward(params, g.shape[0], G.gpu_camera(cam))
+        torch.cuda.synchronize()
+        assert fr.M == 0
+        img = G.np_(fr.img)
+        for c in range(3):
+            assert np.all(img[c] == np.float32(bg[c]))
+        assert np.all(G.np_(fr.T) == 1.0) and np.all(G.np_(fr.last) == 0)
+
+
+def test_pair_capacity_overflow_reports_status():
+    g, cam, _ = U.cfg0_scene()
+    opts = capi.raster_opts()
+    rz = Rasterizer("cuda", opts)
+    params = G.gpu_params(g)
+    gcam = G.gpu_camera(cam)
+    fr = rz.forward(params, g.shape[0], gcam)
+    P = g.shape[0]
+    M = fr.M
+    small = M // 2
+    ws = torch.empty(capi.dg_bin_workspace_size(P, small, rz.n_tiles), dtype=torch.uint8, device="cuda")
+    gid = torch.full((small,), -7, dtype=torch.int32, device="cuda")
+    ranges = torch.full((rz.n_tiles, 2), 5, dtype=torch.int32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    Mdev = torch.zeros(1, dtype=torch.int64, device="cuda")
+    capi.dg_bin_count(rz.depth, rz.tiles, P, ws, ws.numel(), small, rz.n_tiles, Mdev)
+    capi.dg_bin_sort(rz.feat, rz.radius, P, gcam, 16, ws, ws.numel(), small, gid, ranges, status)
+    torch.cuda.synchronize()
+    assert int(Mdev.item()) == M
+    assert int(status.item()) == capi.DG_ERR_CAPACITY
+    assert bool((gid == -7).all()) and bool((ranges == 0).all())
+
+
+def test_host_side_argument_errors():
+    opts = capi.raster_opts(sh_degree=5)
+    cam = G.gpu_camera(synth.camera_cfg0(64, 64, 4.0))
+    t = torch.zeros((59, 4), device="cuda")
+    with pytest.raises(capi.DashGSError) as e:
+        capi.dg_project(t, 4, 4, cam, opts, t, t, t, t, t)
+    assert e.value.status == capi.DG_ERR_ARG and "sh_degree" in str(e.value)
+    with pytest.raises(capi.DashGSError):
+        capi.dg_project(t, 2, 4, cam, capi.raster_opts(), t, t, t, t, t)  # stride < P
+
+
+# ---------------------------------------------------------------- loss, Adam
+def test_loss_l1_parity():
+    rng = np.random.default_rng(5)
+    a = rng.uniform(size=(3, 41, 57)).astype(np.float32)
+    b = rng.uniform(size=(3, 41, 57)).astype(np.float32)
+    b[0, :3, :3] = a[0, :3, :3]
+    ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    n = a.size
+    d = torch.empty_like(ta)
+    loss = torch.zeros(1, device="cuda")
+    ws = torch.empty(capi.dg_loss_workspace_size(n), dtype=torch.uint8, device="cuda")
+    capi.dg_loss_l1(ta, tb, n, d, loss, ws, ws.numel())
+    torch.cuda.synchronize()
+    ol, og = oracle.loss_l1(a.astype(np.float64), b.astype(np.float64))
+    assert abs(loss.item() - ol) <= 1e-6 * ol
+    np.testing.assert_array_equal(G.np_(d), og.astype(np.float32))
+
+
+def test_adam_parity():
+    rng = np.random.default_rng(6)
+    P = 1000 + 3  # ragged tail beyond the 4-wide vector path
+    stride = 1010
+    p = rng.normal(size=(59, stride)).astype(np.float32)
+    lr = np.linspace(1e-4, 1e-2, 59).astype(np.float32)
+    tp = torch.from_numpy(p.copy()).cuda()
+    m = torch.zeros_like(tp); v = torch.zeros_like(tp)
+    op = p[:, :P].astype(np.float64).copy(); om = np.zeros_like(op); ov = np.zeros_like(op)
+    for step in range(1, 6):
+        gr = rng.normal(size=(59, stride)).astype(np.float32)
+        capi.dg_adam_step(tp, torch.from_numpy(gr).cuda(), m, v, stride, P, lr, 0.9, 0.999, 1e-15, step)
+        oracle.adam(op, gr[:, :P].astype(np.float64), om, ov, np.broadcast_to(lr[:, None].astype(np.float64), op.shape).copy(),
+                    0.9, 0.999, 1e-15, step)
+    torch.cuda.synchronize()
+    got = G.np_(tp)
+    np.testing.assert_allclose(got[:, :P], op, rtol=1e-5, atol=1e-6)
+    np.testing.assert_array_equal(got[:, P:], p[:, P:])  # padding untouched
