@@ -81,11 +81,11 @@ def test_cfg0_projection(cfg0):
     np.testing.assert_allclose(f[:, 5], fo[:, 5], rtol=1e-6, atol=1e-7)
     np.testing.assert_allclose(f[:, 6:9], fo[:, 6:9], atol=1e-5)
     np.testing.assert_allclose(G.np_(rz.depth[: g.shape[0]]), pr["depth"], rtol=1e-6)
-    # integer outputs: exact where the FP64 value has a margin to the rounding point
-    r3 = None  # radius = ceil(3 sqrt(lambda)); compare where not within 1e-4 of an integer
+    # integer outputs: radius = ceil(3 sqrt(lambda)) may differ only at a rounding point
     same_r = rec["radius"][vis] == pr["radius"][vis]
     assert same_r.mean() > 0.99
-    np.testing.assert_array_equal(rec["clamp"][vis], np.packbits(pr["clamp"][vis][:, ::-1], axis=1, bitorder="big")[:, 0] >> 5)
+    obits = pr["clamp"][vis].astype(np.int32) @ np.array([1, 2, 4])
+    np.testing.assert_array_equal(rec["clamp"][vis], obits)
 
 
 def test_cfg0_binning_bit_exact(cfg0):
@@ -169,8 +169,9 @@ def test_cfg0_full_gradient_through_autograd(cfg0):
     assert abs(loss.item() - oloss) <= 1e-6
     # the sign pattern of dL/dimg decides the gradient: compare with the oracle's
     # backward fed the GPU's dL (ties |I - target| < 1e-5 may flip)
-    diff = np.abs(G.np_(dL) - odL)
-    assert (diff > 0).mean() < 1e-3
+    flips = np.sign(G.np_(dL)) != np.sign(odL)
+    assert flips.mean() < 1e-3
+    np.testing.assert_allclose(G.np_(dL)[~flips], odL[~flips], rtol=1e-7)
     ob = oracle.backward(g64, ocam, k, of, G.np_(dL).astype(np.float64))
     ok, worst, nbad = G.grad_close(G.np_(params.grad).T, ob["grad"])
     assert ok, (worst, nbad)
