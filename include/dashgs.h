@@ -183,6 +183,22 @@ DG_API size_t dg_loss_workspace_size(int64_t n);
 DG_API dg_status dg_loss_l1(const float* img, const float* target, int64_t n, float* dL_dimg,
                      float* loss, void* ws, size_t ws_bytes, dg_stream stream);
 
+/* L1 loss for callers that cannot allocate device memory (the paper has no
+ * counterpart).  Some callers cannot call cudaMalloc: code inside graph-node or
+ * stream host callbacks, plugins whose host application owns every device
+ * allocation, loops that forbid allocator calls after start-up.  Same result as
+ * dg_loss_l1, but the per-block partial sums live in a fixed 4 KiB device array
+ * inside this library (DG_L1_NOALLOC_BLOCKS floats), so no workspace is passed
+ * and nothing is allocated.  n <= DG_L1_NOALLOC_MAX_N (2^28 values: at most
+ * 1024 values summed per thread), else DG_ERR_ARG.  The first call on a device
+ * looks up the array's device address with that device current (make that
+ * first call before any stream capture).  Every call shares the array: calls
+ * that overlap on the GPU (unordered streams) race on it. */
+#define DG_L1_NOALLOC_BLOCKS 1024
+#define DG_L1_NOALLOC_MAX_N (1024LL * 256LL * 1024LL)
+DG_API dg_status dg_loss_l1_noalloc(const float* img, const float* target, int64_t n, float* dL_dimg,
+                                    float* loss, dg_stream stream);
+
 /* Adam (the optimiser of the 3DGS backbone, supplementary Sec. "Equipping
  * DashGaussian to Backbones"), float32, on all P Gaussians of the planar
  * arrays params/grads/m/v [59][stride].  lr: host array of 59 per-row

@@ -24,7 +24,8 @@ DG_OK, DG_ERR_ARG, DG_ERR_CAPACITY, DG_ERR_TIMEOUT, DG_ERR_CUDA = 0, -1, -2, -3,
 
 EXPORTS = ("dg_last_error", "dg_abi_version", "dg_kernel_launches", "dg_project", "dg_bin_workspace_size", "dg_bin_count",
            "dg_bin_sort", "dg_render_fwd", "dg_render_bwd", "dg_project_bwd", "dg_loss_workspace_size",
-           "dg_loss_l1", "dg_adam_step")
+           "dg_loss_l1", "dg_loss_l1_noalloc", "dg_adam_step")
+L1_NOALLOC_MAX_N = 1024 * 256 * 1024
 
 
 class DashGSError(RuntimeError):
@@ -83,6 +84,7 @@ _SIGS = {
     "dg_project_bwd": ([_P, _I64, _I64, _CAM, _OPT, _P, _P, _P, _P, _P], _ST),
     "dg_loss_workspace_size": ([_I64], _SZ),
     "dg_loss_l1": ([_P, _P, _I64, _P, _P, _P, _SZ, _P], _ST),
+    "dg_loss_l1_noalloc": ([_P, _P, _I64, _P, _P, _P], _ST),
     "dg_adam_step": ([_P, _P, _P, _P, _I64, _I64, _P, _F, _F, _F, _I64, _P], _ST),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -170,8 +172,14 @@ def dg_loss_l1(img, target, n, dL_dimg, loss, ws, ws_bytes, stream=None):
     _check(_lib.dg_loss_l1(_a(img), _a(target), n, _a(dL_dimg), _a(loss), _a(ws), ws_bytes, _s(stream)))
 
 
+def dg_loss_l1_noalloc(img, target, n, dL_dimg, loss, stream=None):
+    """dg_loss_l1 without a workspace: for callers that cannot allocate device memory."""
+    _check(_lib.dg_loss_l1_noalloc(_a(img), _a(target), n, _a(dL_dimg), _a(loss), _s(stream)))
+
+
 def dg_adam_step(params, grads, m, v, stride, P, lr, beta1, beta2, eps, step, stream=None):
     """lr: sequence of 59 per-row learning rates (host)."""
     lr_arr = (ctypes.c_float * NPARAM)(*[float(x) for x in lr])
     _check(_lib.dg_adam_step(_a(params), _a(grads), _a(m), _a(v), stride, P,
                              ctypes.cast(lr_arr, ctypes.c_void_p), beta1, beta2, eps, step, _s(stream)))
+
