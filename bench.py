@@ -199,11 +199,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    torch.cuda.nvtx.range_push("timed")
     t0.record(stream)
     for i in range(args.steps):
         events.clear() if i == 0 else None
         step(args.warmup + i, stage_events=True)
     t1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     launches = capi.dg_kernel_launches() - launches0
     clk = clocks.stop()
