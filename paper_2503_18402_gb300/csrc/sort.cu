@@ -170,15 +170,27 @@ k_rs_hist(const uint32_t* __restrict__ keys, const long long* n_dev, long long n
     for (int d = threadIdx.x; d <= (int)mask; d += RS_THREADS) hist[(long long)d * nblk + blockIdx.x] = h[d];
 }
 
+// Stable scatter of one radix pass.  Ranks are computed per warp-owned
+// segment (match_any within each 32-item round, running per-warp digit
+// counts), the block's items are first placed in shared memory in digit order,
+// then written out so that consecutive threads write consecutive addresses of
+// each digit's run.  kout may be null (values only).
 __global__ void __launch_bounds__(RS_THREADS)
 k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const long long* n_dev,
              long long n_cap, int shift, uint32_t mask, const uint32_t* __restrict__ offs, int nblk)
 {
     __shared__ uint32_t cnt[RS_WARPS][1 << RS_MAXBITS];
+    __shared__ uint32_t dstart[1 << RS_MAXBITS];
+    __shared__ uint32_t gstart[1 << RS_MAXBITS];
+    __shared__ uint32_t sk[RS_TILE];
+    __shared__ uint32_t sv[RS_TILE];
+    __shared__ uint32_t scan_sm[33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long n = eff_count(n_dev, n_cap);
-    const long long seg = (long long)blockIdx.x * RS_TILE + (long long)warp * (32 * RS_IPT);
+    const long long base = (long long)blockIdx.x * RS_TILE;
+    if (base >= n) return;
+    const long long seg = base + (long long)warp * (32 * RS_IPT);
     const int nbins = (int)mask + 1;
     for (int d = lane; d < nbins; d += 32) cnt[warp][d] = 0;
     __syncwarp();
@@ -201,26 +213,40 @@ k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
         __syncwarp();
     }
     __syncthreads();
-    // per-digit exclusive prefix over the warps, plus the block's global offset
-    for (int d = threadIdx.x; d < nbins; d += RS_THREADS) {
-        uint32_t run = offs[(long long)d * nblk + blockIdx.x];
+    // per digit: exclusive prefix over warps (block-local), digit total, global start
+    uint32_t total = 0;
+    if ((int)threadIdx.x < nbins) {
+        const int d = threadIdx.x;
 #pragma unroll
         for (int w = 0; w < RS_WARPS; ++w) {
             const uint32_t c = cnt[w][d];
-            cnt[w][d] = run;
-            run += c;
+            cnt[w][d] = total;
+            total += c;
         }
+        gstart[d] = offs[(long long)d * nblk + blockIdx.x];
     }
+    uint32_t all;
+    const uint32_t ex = block_excl_scan<uint32_t>(total, scan_sm, &all);
+    if ((int)threadIdx.x < nbins) dstart[threadIdx.x] = ex;
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < RS_IPT; ++k) {
         const long long i = seg + (long long)k * 32 + lane;
         if (i < n) {
             const uint32_t d = (key[k] >> shift) & mask;
-            const uint32_t pos = cnt[warp][d] + rank[k];
-            kout[pos] = key[k];
-            vout[pos] = val[k];
+            const uint32_t p = dstart[d] + cnt[warp][d] + rank[k];
+            sk[p] = key[k];
+            sv[p] = val[k];
         }
+    }
+    __syncthreads();
+    const int nvalid = (int)((n - base) < RS_TILE ? (n - base) : RS_TILE);
+    for (int j = threadIdx.x; j < nvalid; j += RS_THREADS) {
+        const uint32_t kk = sk[j];
+        const uint32_t d = (kk >> shift) & mask;
+        const uint32_t pos = gstart[d] + (uint32_t)j - dstart[d];
+        if (kout) kout[pos] = kk;
+        vout[pos] = sv[j];
     }
 }
 
@@ -231,13 +257,15 @@ struct SortBufs {
 
 // Stable LSD sort of (key, val) over the low `bits` key bits.  Input in
 // (k0, v0); (k1, v1) is ping-pong space.  The last pass writes to
-// (kfin, vfin) when given (they must not alias k0/k1, v0/v1), else to the
-// ping-pong buffer whose turn it is.  Returns where the result lies.
+// (kfin, vfin) when vfin is given (kfin may then be null: values only; they
+// must not alias k0/k1, v0/v1), else to the ping-pong buffer whose turn it
+// is.  When hist0_ready, the caller already wrote pass 0's per-block
+// histogram into sb.hist.  Returns where the result lies.
 struct KV { uint32_t* k; uint32_t* v; };
 
 static KV radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* kfin,
                      uint32_t* vfin, const long long* n_dev, long long n_cap, int bits,
-                     const SortBufs& sb, cudaStream_t s)
+                     const SortBufs& sb, cudaStream_t s, bool hist0_ready = false)
 {
     const int nblk = (int)((n_cap + RS_TILE - 1) / RS_TILE);
     if (nblk == 0) return KV{k0, v0};
@@ -254,10 +282,12 @@ static KV radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uin
         const int b = (bits - shift) < per ? (bits - shift) : per;
         const uint32_t mask = (1u << b) - 1u;
         const bool last = p == npass - 1;
-        uint32_t* kd = (last && kfin) ? kfin : (ks == k0 ? k1 : k0);
+        uint32_t* kd = (last && vfin) ? kfin : (ks == k0 ? k1 : k0);
         uint32_t* vd = (last && vfin) ? vfin : (vs == v0 ? v1 : v0);
-        k_rs_hist<<<nblk, RS_THREADS, 0, s>>>(ks, n_dev, n_cap, shift, mask, sb.hist, nblk);
-        dg_note_launch();
+        if (!(p == 0 && hist0_ready)) {
+            k_rs_hist<<<nblk, RS_THREADS, 0, s>>>(ks, n_dev, n_cap, shift, mask, sb.hist, nblk);
+            dg_note_launch();
+        }
         const long long nh = (long long)(mask + 1) * nblk;
         exclusive_scan(LoadU32{sb.hist}, nh, sb.hist, sb.bsum, (long long*)nullptr, s);
         k_rs_scatter<<<nblk, RS_THREADS, 0, s>>>(ks, vs, kd, vd, n_dev, n_cap, shift, mask, sb.hist, nblk);
@@ -266,6 +296,15 @@ static KV radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uin
         vs = vd;
     }
     return KV{ks, vs};
+}
+
+// Digit width of the first pass of radix_sort over `bits` bits.
+static int first_pass_bits(int bits)
+{
+    if (bits == 0) return 0;
+    const int npass = (bits + RS_MAXBITS - 1) / RS_MAXBITS;
+    const int per = (bits + npass - 1) / npass;
+    return bits < per ? bits : per;
 }
 
 // --------------------------------------------------------------- binning
@@ -278,42 +317,120 @@ __global__ void k_depth_keys(const float* __restrict__ depth, const int* __restr
     idx[i] = (uint32_t)i;
 }
 
-__global__ void k_emit(const float4* __restrict__ feat, const int* __restrict__ radius,
-                       const uint32_t* __restrict__ order,
-                       const uint64_t* __restrict__ poff, int P, const long long* M_dev, long long M_cap,
-                       int B, int TX, int TY, uint32_t* __restrict__ pkey, uint32_t* __restrict__ pval,
-                       int* status)
+// First sorted position whose pair range holds each RS_TILE block's first pair.
+__global__ void k_block_starts(const uint64_t* __restrict__ poff, int P, const long long* M_dev, long long M_cap,
+                               int* __restrict__ bstart)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const long long M = *M_dev;
+    if (s >= P || M > M_cap) return;
+    const long long a = (long long)poff[s];
+    const long long e = s + 1 < P ? (long long)poff[s + 1] : M;
+    if (e <= a) return;
+    for (long long b = (a + RS_TILE - 1) / RS_TILE; b * RS_TILE < e; ++b) bstart[b] = s;
+}
+
+// Pair emission, one RS_TILE block of consecutive pairs per CTA.  The block's
+// Gaussians (at most RS_TILE, all with >= 1 pair) are staged in shared memory
+// with their rects; each pair finds its Gaussian by binary search over the
+// staged starts.  Writes key = tile id and value = Gaussian index, coalesced,
+// and the per-block histogram of the first radix digit.
+__global__ void __launch_bounds__(RS_THREADS)
+k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const uint32_t* __restrict__ order,
+       const uint64_t* __restrict__ poff, const int* __restrict__ bstart, int P, const long long* M_dev,
+       long long M_cap, int B, int TX, int TY, uint32_t mask0, uint32_t* __restrict__ pkey,
+       uint32_t* __restrict__ pval, uint32_t* __restrict__ hist0, int nblk, int* status)
+{
+    __shared__ int w_start[RS_TILE];      // pair offset of each staged Gaussian, relative to the block
+    __shared__ uint32_t w_xy[RS_TILE];    // rect x0 | y0 << 16
+    __shared__ int w_wx[RS_TILE];         // rect width in tiles
+    __shared__ uint32_t w_g[RS_TILE];     // Gaussian index
+    __shared__ uint32_t h[1 << RS_MAXBITS];
+    const long long M = *M_dev;
     if (M > M_cap) {
-        if (s == 0) *status = DG_ERR_CAPACITY;
+        if (blockIdx.x == 0 && threadIdx.x == 0) *status = DG_ERR_CAPACITY;
         return;
     }
-    if (s == 0) *status = DG_OK;
-    if (s >= P) return;
-    const uint32_t g = order[s];
-    if (radius[g] == 0) return;
-    const float4 f0 = feat[3 * (size_t)g];
-    const Rect q = tile_rect(f0.x, f0.y, radius[g], B, TX, TY);
-    uint64_t o = poff[s];
-    for (int ty = q.y0; ty < q.y1; ++ty)
-        for (int tx = q.x0; tx < q.x1; ++tx) {
-            pkey[o] = (uint32_t)(ty * TX + tx);
-            pval[o] = g;
-            ++o;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *status = DG_OK;
+    __shared__ int s_nw;
+    for (int d = threadIdx.x; d < (1 << RS_MAXBITS); d += RS_THREADS) h[d] = 0;
+    if (threadIdx.x == 0) s_nw = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * RS_TILE;
+    if (base < M) {  // block-uniform
+        const long long end = (base + RS_TILE) < M ? (base + RS_TILE) : M;
+        const int s_lo = bstart[blockIdx.x];
+        // stage the Gaussians whose pair range starts before `end` (a prefix of s_lo, s_lo+1, ...)
+        int top = 0;
+        for (int w = threadIdx.x; w < RS_TILE; w += RS_THREADS) {
+            const int s = s_lo + w;
+            if (s >= P) break;
+            const long long st = (long long)poff[s];
+            if (st >= end) break;
+            const uint32_t g = order[s];
+            const float4 f0 = feat[3 * (size_t)g];
+            const Rect q = tile_rect(f0.x, f0.y, radius[g], B, TX, TY);
+            w_start[w] = (int)(st - base);
+            w_xy[w] = (uint32_t)q.x0 | ((uint32_t)q.y0 << 16);
+            w_wx[w] = q.x1 - q.x0;
+            w_g[w] = g;
+            top = w + 1;
         }
+        if (top > 0) atomicMax(&s_nw, top);
+        __syncthreads();
+        const int nw = s_nw;
+#pragma unroll 2
+        for (int k = 0; k < RS_IPT; ++k) {
+            const long long i = base + (long long)k * RS_THREADS + threadIdx.x;
+            if (i >= end) break;
+            const int rel = (int)(i - base);
+            int lo = 0, hi = nw - 1;  // w_start[0] <= 0 <= rel
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (w_start[mid] <= rel) lo = mid; else hi = mid - 1;
+            }
+            const int j = rel - w_start[lo];
+            const int wx = w_wx[lo];
+            const uint32_t xy = w_xy[lo];
+            const int ty = (int)(xy >> 16) + j / wx;
+            const int tx = (int)(xy & 0xffffu) + j % wx;
+            const uint32_t key = (uint32_t)(ty * TX + tx);
+            pkey[i] = key;
+            pval[i] = w_g[lo];
+            atomicAdd(&h[key & mask0], 1u);
+        }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d <= (int)mask0; d += RS_THREADS) hist0[(long long)d * nblk + blockIdx.x] = h[d];
 }
 
 __global__ void k_ranges(const uint32_t* __restrict__ keys, const long long* M_dev, long long M_cap,
                          uint2* __restrict__ ranges)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long M = eff_count(M_dev, M_cap);
-    if (i >= M) return;
-    const uint32_t t = keys[i];
-    if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
-    if (i == M - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+    const long long nq = (M + 3) / 4;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long i0 = 4 * q;
+        uint32_t k[4];
+        if (i0 + 3 < M) {
+            const uint4 v = *(const uint4*)(keys + i0);
+            k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+        } else {
+            for (int c = 0; c < 4; ++c) k[c] = i0 + c < M ? keys[i0 + c] : 0xffffffffu;
+        }
+        uint32_t prev = i0 > 0 ? keys[i0 - 1] : 0xffffffffu;
+        const uint32_t next = i0 + 4 < M ? keys[i0 + 4] : 0xffffffffu;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const long long i = i0 + c;
+            if (i >= M) break;
+            const uint32_t nx = c < 3 ? k[c + 1] : next;
+            if (i == 0 || prev != k[c]) ranges[k[c]].x = (uint32_t)i;
+            if (i == M - 1 || nx != k[c]) ranges[k[c]].y = (uint32_t)(i + 1);
+            prev = k[c];
+        }
+    }
 }
 
 // Workspace layout (offsets 256-byte aligned).  The pair count and the
@@ -326,6 +443,7 @@ struct BinWs {
     uint64_t* poff;                     // P pair offsets
     uint32_t *pk0, *pv0, *pk1, *pv1;   // pair sort, M_cap each
     uint32_t* pkfin;                    // sorted pair keys, M_cap
+    int* bstart;                        // first sorted position of each pair block
     uint32_t* hist;
     uint64_t* bsum;
     size_t bytes;
@@ -345,6 +463,7 @@ static BinWs bin_layout(char* base, long long P, long long M_cap)
     w.pk0 = (uint32_t*)take(4 * M_cap); w.pv0 = (uint32_t*)take(4 * M_cap);
     w.pk1 = (uint32_t*)take(4 * M_cap); w.pv1 = (uint32_t*)take(4 * M_cap);
     w.pkfin = (uint32_t*)take(4 * M_cap);
+    w.bstart = (int*)take(4 * ((M_cap + RS_TILE - 1) / RS_TILE + 1));
     const long long n = P > M_cap ? P : M_cap;
     const long long nblk = (n + RS_TILE - 1) / RS_TILE;
     const long long nh = (long long)(1 << RS_MAXBITS) * nblk;
@@ -408,18 +527,28 @@ extern "C" dg_status dg_bin_sort(const float* feat, const int32_t* radius, int64
     cudaStream_t s = (cudaStream_t)stream;
     cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * n_tiles, s);
     cudaMemsetAsync(status, 0, sizeof(int32_t), s);
-    const int eb = (int)((P + 255) / 256);
-    // emit in depth order (pair count and slots from phase 1), or flag overflow
-    dg::k_emit<<<eb > 0 ? eb : 1, 256, 0, s>>>((const float4*)feat, radius, w.dv0, w.poff, (int)P, w.M,
-                                                M_cap, tile, TX, TY, w.pk0, w.pv0, status);
-    dg_note_launch();
-    if (M_cap == 0) return dg_check_launch("bin_sort");
     int bits = 0;
     while ((1ll << bits) < n_tiles) ++bits;
+    const int b0 = dg::first_pass_bits(bits);
+    const uint32_t mask0 = b0 > 0 ? (1u << b0) - 1u : 0u;
+    const int nblk = (int)((M_cap + dg::RS_TILE - 1) / dg::RS_TILE);
+    const int pb = (int)((P + 255) / 256);
+    if (P > 0 && nblk > 0) {
+        dg::k_block_starts<<<pb, 256, 0, s>>>(w.poff, (int)P, w.M, M_cap, w.bstart);
+        dg_note_launch();
+    }
+    // emit pairs in depth order (slots from phase 1) with pass-0 histogram, or flag overflow
+    dg::k_emit<<<nblk > 0 ? nblk : 1, dg::RS_THREADS, 0, s>>>((const float4*)feat, radius, w.dv0, w.poff, w.bstart,
+                                                            (int)P, w.M, M_cap, tile, TX, TY, mask0, w.pk0, w.pv0,
+                                                            w.hist, nblk > 0 ? nblk : 1, status);
+    dg_note_launch();
+    if (M_cap == 0) return dg_check_launch("bin_sort");
     dg::SortBufs sb{w.hist, w.bsum};
-    dg::radix_sort(w.pk0, w.pv0, w.pk1, w.pv1, w.pkfin, gid, w.M, M_cap, bits, sb, s);
-    const int rb = (int)((M_cap + 255) / 256);
-    dg::k_ranges<<<rb, 256, 0, s>>>(w.pkfin, w.M, M_cap, (uint2*)ranges);
+    dg::radix_sort(w.pk0, w.pv0, w.pk1, w.pv1, w.pkfin, gid, w.M, M_cap, bits, sb, s, /*hist0_ready=*/bits > 0);
+    const long long nq = (M_cap + 3) / 4;
+    long long rb = (nq + 255) / 256;
+    if (rb > 152 * 32) rb = 152 * 32;
+    dg::k_ranges<<<(int)(rb > 0 ? rb : 1), 256, 0, s>>>(w.pkfin, w.M, M_cap, (uint2*)ranges);
     dg_note_launch();
     return dg_check_launch("bin_sort");
 }

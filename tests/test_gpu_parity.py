@@ -290,3 +290,72 @@ def test_adam_parity():
     got = G.np_(tp)
     np.testing.assert_allclose(got[:, :P], op, rtol=1e-5, atol=1e-6)
     np.testing.assert_array_equal(got[:, P:], p[:, P:])  # padding untouched
+
+
+# ---------------------------------------------------------------- full size, sampled
+@pytest.fixture(scope="module")
+def fullsize():
+    """The bench's workload: 2M-Gaussian textured scene, one 1237x822 view."""
+    gt = synth.textured_scene(2_000_000, 1001)
+    model = synth.jitter(gt, 3001)
+    view = synth.ring_cameras(160, 1237, 822, 5.0, 2001)[0]
+    rz = Rasterizer("cuda", capi.raster_opts())
+    params = G.gpu_params(model)
+    gcam = G.gpu_camera(view)
+    fr = rz.forward(params, model.shape[0], gcam, examined=True)
+    torch.cuda.synchronize()
+    return model, view, rz, params, gcam, fr
+
+
+def test_fullsize_sampled_tiles_and_pixels(fullsize):
+    model, view, rz, params, gcam, fr = fullsize
+    P, W, H = model.shape[0], 1237, 822
+    rec = _records(rz, P)
+    gid, ranges = _gpu_bins(rz, fr)
+    assert fr.M > 10_000_000 and int(rec["tiles"].sum()) == fr.M
+    # ranges partition [0, M) in tile order
+    nz = ranges[:, 1] > ranges[:, 0]
+    assert ranges[nz, 0].min() == 0 and ranges[nz, 1].max() == fr.M
+    assert int((ranges[:, 1] - ranges[:, 0]).sum()) == fr.M
+    rng = np.random.default_rng(7)
+    n_tiles = ranges.shape[0]
+    tiles = np.concatenate([[0, n_tiles - 1, 77], rng.choice(n_tiles, 21, replace=False)])
+    k = oracle.consts()
+    for t in tiles:
+        ref = oracle.tile_list(rec["uv"], rec["radius"], rec["key"], W, H, 16, int(t))
+        s, e = ranges[t]
+        np.testing.assert_array_equal(gid[s:e], ref)
+    # sampled pixels (including the ragged last row/column) against Eq. 1
+    px = np.concatenate([[0, W - 1, W - 1, 0], rng.integers(0, W, 300)])
+    py = np.concatenate([[0, 0, H - 1, H - 1], rng.integers(0, H, 300)])
+    o = oracle.render_pixels(rec["feat"], W, 16, gid, ranges, np.zeros(3), k, px, py)
+    img = G.np_(fr.img)
+    assert np.abs(img[:, py, px].T - o["rgb"]).max() <= 1e-5
+    assert np.abs(G.np_(fr.T)[py, px] - o["T"]).max() <= 1e-5
+    np.testing.assert_array_equal(G.np_(fr.last)[py, px], o["last"])
+    np.testing.assert_array_equal(G.np_(rz.examined)[py, px], o["examined"])
+
+
+def test_fullsize_backward_on_sampled_tiles(fullsize):
+    model, view, rz, params, gcam, fr = fullsize
+    P, W, H = model.shape[0], 1237, 822
+    rec = _records(rz, P)
+    gid, ranges = _gpu_bins(rz, fr)
+    # dL/dimg non-zero only on a few tiles: the oracle's adjoint then touches only them
+    rng = np.random.default_rng(8)
+    dL = np.zeros((3, H, W), np.float32)
+    TX = (W + 15) // 16
+    for t in rng.choice(ranges.shape[0], 6, replace=False):
+        ty, tx = divmod(int(t), TX)
+        ys, xs = slice(ty * 16, min(H, ty * 16 + 16)), slice(tx * 16, min(W, tx * 16 + 16))
+        hh, ww = ys.stop - ys.start, xs.stop - xs.start
+        dL[:, ys, xs] = rng.normal(size=(3, hh, ww)).astype(np.float32) / 3e6
+    grads = torch.empty_like(params)
+    rz.backward(params, fr, torch.from_numpy(dL).cuda(), grads)
+    torch.cuda.synchronize()
+    g2 = G.np_(rz.grad2d[:P])[:, :9]
+    og2 = oracle.render_bwd(rec["feat"], W, H, 16, gid, ranges, np.zeros(3), oracle.consts(), dL.astype(np.float64))
+    ok, worst, nbad = G.grad_close(g2, og2, atol=1e-9)
+    assert ok, (worst, nbad)
+    touched = np.abs(og2).sum(1) > 0
+    assert touched.sum() > 1000
