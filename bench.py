@@ -34,8 +34,8 @@ sys.path.insert(0, ROOT)
 W_FULL, H_FULL = 1237, 822
 N_GAUSS = 2_000_000
 N_VIEWS = 16
-FLOPS_FWD = 22     # FP32 flops per examined (pixel, Gaussian) entry, forward
-FLOPS_BWD = 58     # FP32 flops per back-traversed entry, backward
+FLOPS_FWD = 22     # FP32 flops per blended (pixel, Gaussian) entry, forward
+FLOPS_BWD = 58     # FP32 flops per blended entry, backward (every blended entry is revisited)
 SM_COUNT, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
 
 
@@ -155,7 +155,7 @@ def run_ours(args):
     for c in gcams:
         fr = rz.forward(params, P, c, examined=True)
         E_f.append(int(rz.examined.sum().item()))
-        E_b.append(int(fr.last.sum().item()))
+        E_b.append(int(rz.blended.sum().item()))
         M_tot.append(fr.M)
 
     events = []
@@ -261,7 +261,7 @@ def run_ours(args):
     out["stages"] = stages
     pf = sum(E_f) / len(E_f)
     pb = sum(E_b) / len(E_b)
-    work = {"render_fwd": ("alu", pf * FLOPS_FWD), "render_bwd": ("alu", pb * FLOPS_BWD),
+    work = {"render_fwd": ("alu", pb * FLOPS_FWD), "render_bwd": ("alu", pb * FLOPS_BWD),
             "project": ("hbm", P * 297.0), "project_bwd": ("hbm", P * 525.0), "adam": ("hbm", P * 1652.0)}
     dom = max((k for k in stages if k in work), key=lambda k: stages[k]["ms"])
     kind, units = work[dom]
@@ -283,8 +283,8 @@ def run_ours(args):
         out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                            "frac": round(ach / hbm, 4), "traffic": None,
                            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s"}
-    out["work"] = {"pairs_per_view": int(sum(M_tot) / len(M_tot)), "examined_fwd_per_view": int(pf),
-                   "traversed_bwd_per_view": int(pb)}
+    out["work"] = {"pairs_per_view": int(sum(M_tot) / len(M_tot)), "examined_per_view": int(pf),
+                   "blended_per_view": int(pb)}
     out["fwd_bwd_ms_per_view"] = round(sum(stages[k]["ms"] for k in stages if k not in ("adam", "loss")), 4)
     out["e2e"] = {"value": round(e2e_ms / views_total, 4), "unit": "ms/view",
                   "h2d_bytes_per_step": int(targets[0].numel() * 4), "d2h_bytes_per_step": 4 + 8}

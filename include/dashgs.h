@@ -75,16 +75,20 @@ typedef struct dg_camera {
     int32_t width, height;
 } dg_camera;
 
-/* Rasterizer options.  tile: tile edge B in pixels (16); sh_degree: 0..3;
- * near_plane: Gaussians with camera z <= near_plane are culled (0.2);
- * eps2d: dilation added to the 2D covariance diagonal, px^2 (0.3);
- * bg: background colour composited with the final transmittance. */
+/* Rasterizer options.  tile: tile edge B in pixels (16; the render kernels
+ * take 8 or 16); sh_degree: 0..3; near_plane: Gaussians with camera z <=
+ * near_plane are culled (0.2); eps2d: dilation added to the 2D covariance
+ * diagonal, px^2 (0.3); bg: background colour composited with the final
+ * transmittance; pixels_per_thread: pixels each render thread owns (1, 2 or
+ * 4 with tile 16; 0 = the library's default per pass).  It changes the launch
+ * shape only, not the result beyond float summation order. */
 typedef struct dg_raster_opts {
     int32_t tile;
     int32_t sh_degree;
     float near_plane;
     float eps2d;
     float bg[3];
+    int32_t pixels_per_thread;
 } dg_raster_opts;
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
@@ -148,10 +152,12 @@ DG_API dg_status dg_bin_sort(const float* feat, const int32_t* radius, int64_t P
  * Out: img [3][H][W] float32 (planar RGB), T_final [H][W] float32,
  *      last [H][W] int32 = 1-based list position of the last blended Gaussian
  *      (0 if none), examined [H][W] int32 (nullable) = list entries visited
- *      including the one that stopped compositing. */
+ *      including the one that stopped compositing, blended [H][W] int32
+ *      (nullable) = entries blended into the pixel. */
 DG_API dg_status dg_render_fwd(const float* feat, const uint32_t* gid, const uint32_t* ranges,
                         const dg_camera* cam, const dg_raster_opts* opts, float* img,
-                        float* T_final, int32_t* last, int32_t* examined, dg_stream stream);
+                        float* T_final, int32_t* last, int32_t* examined, int32_t* blended,
+                        dg_stream stream);
 
 /* Adjoint of Eq. 1 ("fully differentiable", Sec. 3).  Recomputes each
  * pixel's transmittance back to front from T_final and last (no per-pair
@@ -183,6 +189,17 @@ DG_API size_t dg_loss_workspace_size(int64_t n);
 DG_API dg_status dg_loss_l1(const float* img, const float* target, int64_t n, float* dL_dimg,
                      float* loss, void* ws, size_t ws_bytes, dg_stream stream);
 
+/* Mean squared error of two arrays (held-out PSNR = -10 log10(mse) for images
+ * in [0, 1]; Sec. 5 "Metrics").  ws: dg_loss_workspace_size(n) bytes. */
+DG_API dg_status dg_mse(const float* a, const float* b, int64_t n, float* mse, void* ws, size_t ws_bytes,
+                        dg_stream stream);
+
+/* Opacity reset of the 3DGS backbone (kept unchanged by the paper, Sec. 5):
+ * opacity logit <- min(logit, logit(max_opacity)) and its Adam moments set
+ * to zero, for Gaussians 0..P-1 of the planar arrays. */
+DG_API dg_status dg_opacity_reset(float* params, float* m, float* v, int64_t stride, int64_t P, float max_opacity,
+                                  dg_stream stream);
+
 /* L1 loss for callers that cannot allocate device memory (the paper has no
  * counterpart).  Some callers cannot call cudaMalloc: code inside graph-node or
  * stream host callbacks, plugins whose host application owns every device
@@ -207,6 +224,123 @@ DG_API dg_status dg_loss_l1_noalloc(const float* img, const float* target, int64
 DG_API dg_status dg_adam_step(float* params, const float* grads, float* m, float* v, int64_t stride,
                        int64_t P, const float* lr, float beta1, float beta2, float eps,
                        int64_t step, dg_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* Scheduled densification (supplementary "Densification of DashGaussian"):
+ * prune first (N'), then clone or split the Gaussians that meet the 3DGS
+ * condition (mean view-space positional gradient >= grad_thresh) and have a
+ * top-(P_i - N') score; P_i comes from dg_schedule_densify (Eq. 4/5).
+ * Selected Gaussians whose largest scale exceeds percent_dense * extent are
+ * split into two samples (scales / 1.6, means drawn with caller-provided
+ * standard normal noise), the others are cloned.  All integer decisions are
+ * float32 comparisons against float32 thresholds (logit of min_opacity, log
+ * of the scale limits).  Ties in the top-k go to the lower index; survivors
+ * keep their order, new Gaussians follow in index order of their source and
+ * start with zero Adam moments. */
+typedef struct dg_densify_opts {
+    float grad_thresh;        /* 0.0002 */
+    float min_opacity;        /* 0.005: pruned below */
+    float percent_dense;      /* 0.01 */
+    float extent;             /* scene extent */
+    float max_screen_radius;  /* > 0: also prune when the largest radius seen exceeds it */
+    float max_world_scale;    /* > 0: also prune when the largest scale exceeds it */
+} dg_densify_opts;
+
+/* After each rendered view: for Gaussians with radius > 0,
+ * grad_accum += |(dL/du W/2, dL/dv H/2)| (the NDC-space gradient norm),
+ * denom += 1, max_radius = max(max_radius, radius).  All [P] float32. */
+DG_API dg_status dg_densify_stats(const float* grad2d, const int32_t* radius, int64_t P, int32_t W, int32_t H,
+                                  float* grad_accum, float* denom, float* max_radius, dg_stream stream);
+DG_API size_t dg_densify_workspace_size(int64_t P);
+/* Phase 1: prune/candidate/split flags into ws; counts (device int64[2]) =
+ * {N' kept, candidates}.  The caller reads the counts (Eq. 5's P_add is the
+ * candidate count) before phase 2 with the same ws. */
+DG_API dg_status dg_densify_mark(const float* params, int64_t stride, int64_t P, const float* grad_accum,
+                                 const float* denom, const float* max_radius, const dg_densify_opts* opts,
+                                 void* ws, size_t ws_bytes, int64_t* counts, dg_stream stream);
+/* Phase 2: selects min(n_cand, budget) candidates, writes survivors and new
+ * Gaussians to dst (planar [59][dst_stride], dst_stride >= P + min(n_cand,
+ * budget)) and their Adam moments; noise [min(n_cand,budget)][2][3] standard
+ * normals for the j-th selected Gaussian (index order); *P_out (device int64)
+ * = N' + number selected.  Sources and destinations must not overlap. */
+DG_API dg_status dg_densify_apply(const float* params, const float* m, const float* v, int64_t stride, int64_t P,
+                                  int64_t n_cand, int64_t budget, const float* noise, void* ws, size_t ws_bytes,
+                                  float* dst_params, float* dst_m, float* dst_v, int64_t dst_stride,
+                                  int64_t* P_out, dg_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* Resolution schedule (Sec. 4.1-4.2, Eq. 2, supplementary Eq. 6/7, floor
+ * modulation of Sec. 5) and primitive schedule (Sec. 4.3, Eq. 4/5).
+ *
+ * Spectrum of the training views (once per scene, FP64 sums on the GPU):
+ *   for each view: dg_spectrum_accumulate(view [3][H][W] float32, ...) adds
+ *   sum over RGB of |DFT2(view_c)| into acc [H][W] float64 (caller zeroes acc
+ *   before the first view); then dg_spectrum_finalize divides by n_views,
+ *   moves DC to (H/2, W/2) into shifted [H][W] float64 and writes the summed-
+ *   area table sat [(H+1)][(W+1)] float64 (sat[y][x] = sum of shifted over
+ *   rows < y, columns < x).  ws: dg_spectrum_workspace_size(H, W) bytes. */
+DG_API size_t dg_spectrum_workspace_size(int32_t H, int32_t W);
+DG_API dg_status dg_spectrum_accumulate(const float* view, int32_t H, int32_t W, double* acc, void* ws,
+                                        size_t ws_bytes, dg_stream stream);
+DG_API dg_status dg_spectrum_finalize(const double* acc, int32_t n_views, int32_t H, int32_t W,
+                                      double* shifted, double* sat, dg_stream stream);
+
+/* Anti-aliased ground-truth downsampling (supplementary "Ground Truth
+ * Downsampling"), read as area resampling with exact coverage weights:
+ * src [C][H][W] -> dst [C][h][w], h <= H, w <= W. */
+DG_API dg_status dg_downsample_area(const float* src, int32_t C, int32_t H, int32_t W, float* dst,
+                                    int32_t h, int32_t w, dg_stream stream);
+
+#define DG_SCHED_MAX_LEVELS 64
+
+/* Host-side schedule parameters.  S: total iterations; a: X(F_rm) = X(F)/a
+ * (4); m: number of levels (<= 0: ceil(r_m)); gamma, eta: Eq. 5 (0.98, 1);
+ * P_init: initial primitive count; P_cap: hard cap on the primitive target
+ * (<= 0: none); lr_pos_init/final: position learning rate held, then decayed
+ * from the first full-resolution iteration to S. */
+typedef struct dg_sched_params {
+    int64_t S;
+    double a;
+    int32_t m;
+    double gamma, eta;
+    double P_init, P_cap;
+    double lr_pos_init, lr_pos_final;
+} dg_sched_params;
+
+/* Schedule state (host struct).  X[i], r[i], s[i] for i = 0..m: level
+ * significance, downsampling factor and anchor iteration (s[0] = S, s[m] = 0);
+ * k_full: first iteration with floor(r) = 1; P_fin: Eq. 5 state. */
+typedef struct dg_schedule {
+    dg_sched_params p;
+    int32_t H, W, m;
+    double X0, Xm, r_m;
+    double X[DG_SCHED_MAX_LEVELS + 1], r[DG_SCHED_MAX_LEVELS + 1], s[DG_SCHED_MAX_LEVELS + 1];
+    int64_t k_full;
+    double P_fin;
+} dg_schedule;
+
+/* Per-iteration outputs: continuous and floored factor, render size
+ * (floor(H/r_mod), floor(W/r_mod)), position learning rate, Eq. 4 target. */
+typedef struct dg_sched_out {
+    double r_cont;
+    int32_t r_mod, height, width;
+    double lr_pos;
+    double P_target;
+} dg_sched_out;
+
+/* Builds the schedule from the HOST copy of the summed-area table (host call,
+ * no device work): X(r) = centred (floor(H/r) x floor(W/r)) crop sum / (H W)
+ * (Eq. 2 with a pixel-normalised DFT, which absorbs the 1/r^2 of Sec. 4.1);
+ * r_m = inf{r : X(r) <= X(1)/a}; X_i linear between X(1) and X(1)/a;
+ * r_i = inf{r : X(r) <= X_i}; s_i = S ln(X_i/X_m) / ln(X_0/X_m) (Eq. 7);
+ * P_fin = 5 P_init. */
+DG_API dg_status dg_schedule_init(const double* sat_host, int32_t H, int32_t W, const dg_sched_params* p,
+                                  dg_schedule* out);
+/* Rendering factor, size, learning rate and Eq. 4 target at `iter` (host). */
+DG_API dg_status dg_schedule_step(const dg_schedule* s, int64_t iter, dg_sched_out* out);
+/* Densification step: Eq. 5 update of P_fin with P_add, then as
+ * dg_schedule_step (host). */
+DG_API dg_status dg_schedule_densify(dg_schedule* s, int64_t iter, int64_t P_add, dg_sched_out* out);
 
 #ifdef __cplusplus
 }

@@ -91,7 +91,7 @@ def lib():
         L.dgo_bin.argtypes = [_I64, _P, _P, _P, _I32, _I32, _I32, _I64, _P, _P, _P]
         L.dgo_bin.restype = _I64
         L.dgo_render_fwd.argtypes = [_P, _I32, _I32, _I32, _P, _P, _P, ctypes.POINTER(Consts),
-                                     _P, _P, _P, _P]
+                                     _P, _P, _P, _P, _P]
         L.dgo_render_bwd.argtypes = [_P, _I32, _I32, _I32, _P, _P, _P, ctypes.POINTER(Consts),
                                      _P, _P]
         L.dgo_project_bwd.argtypes = [_I64, _P, ctypes.POINTER(Camera), ctypes.POINTER(Consts),
@@ -198,9 +198,10 @@ def render_fwd(feat, W, H, B, gid, ranges, bg, k: Consts) -> dict:
     T = np.zeros((H, W))
     last = np.zeros((H, W), np.int32)
     ex = np.zeros((H, W), np.int32)
+    bl = np.zeros((H, W), np.int32)
     lib().dgo_render_fwd(_ptr(feat), W, H, B, _ptr(gid), _ptr(ranges), _ptr(bg),
-                         ctypes.byref(k), _ptr(img), _ptr(T), _ptr(last), _ptr(ex))
-    return dict(img=img, T=T, last=last, examined=ex)
+                         ctypes.byref(k), _ptr(img), _ptr(T), _ptr(last), _ptr(ex), _ptr(bl))
+    return dict(img=img, T=T, last=last, examined=ex, blended=bl)
 
 
 def render_bwd(feat, W, H, B, gid, ranges, bg, k: Consts, dL_dimg) -> np.ndarray:

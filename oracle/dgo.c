@@ -419,19 +419,21 @@ static int64_t composite_pixel(const double* feat, int32_t W, int32_t B, const u
 
 void dgo_render_fwd(const double* feat, int32_t W, int32_t H, int32_t B, const uint32_t* gid,
                     const uint32_t* ranges, const double* bg, const dgo_consts* k,
-                    double* img, double* T_out, int32_t* last_out, int32_t* examined_out)
+                    double* img, double* T_out, int32_t* last_out, int32_t* examined_out,
+                    int32_t* blended_out)
 {
     const int64_t HW = (int64_t)W * H;
     for (int32_t py = 0; py < H; ++py)
         for (int32_t px = 0; px < W; ++px) {
             double T, C[3];
             int32_t last, ex;
-            composite_pixel(feat, W, B, gid, ranges, k, px, py, &T, &last, &ex, C, NULL);
+            const int64_t nb = composite_pixel(feat, W, B, gid, ranges, k, px, py, &T, &last, &ex, C, NULL);
             const int64_t i = (int64_t)py * W + px;
             for (int ch = 0; ch < 3; ++ch) img[ch * HW + i] = C[ch] + T * bg[ch];
             T_out[i] = T;
             last_out[i] = last;
             if (examined_out) examined_out[i] = ex;
+            if (blended_out) blended_out[i] = (int32_t)nb;
         }
 }
 

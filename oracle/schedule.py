@@ -8,15 +8,19 @@ Follows the paper's steps in its notation:
     (floor(H/r), floor(W/r)); the crop keeps frequencies
     [-floor(h/2), ceil(h/2) - 1] around DC.
   * Eq. 2: X(F_r) = mean over views of the summed DFT magnitudes of the
-    downsampled view, so X(r) = r^-2 * sum_{crop(r)} Mbar, Mbar the view mean
-    of sum over RGB channels of |DFT(I_ch)| (the paper's I has one channel;
-    the channels are summed).
+    downsampled view.  Reading: the DFT is normalised by the pixel count, so
+    the 1/r^2 of Sec. 4.1 (which relates unnormalised transforms) cancels and
+    X(r) = sum_{crop(r)} Mbar / (H W), Mbar the view mean of the sum over RGB
+    channels of |DFT(I_ch)| (the paper's I has one channel; the channels are
+    summed).  With unnormalised transforms X(r) <= X(1)/r^2 for every image,
+    so r_m could never exceed sqrt(a) = 2 and the floor modulation would keep
+    full resolution throughout, contrary to Sec. 5.3 and the role of a.
   * Sec. 4.2: r_m is where X(F_rm) = X(F)/a (a = 4); X_1..X_{m-1} are
     spaced linearly between X(F) and X(F_rm); r_i solves X(F_ri) = X_i.
-    X(r) is piecewise continuous and non-increasing, so "solves" is read as
+    X(r) is a non-increasing step function of r, so "solves" is read as
     r_i = inf{r >= 1 : X(r) <= X_i}, found exactly by walking the intervals
-    between crop-size breakpoints.  m is not given by the paper; the default
-    reading is m = ceil(r_m).
+    between crop-size breakpoints (it is always a breakpoint H/n or W/n).  m is not given by the paper; the default
+    reading is m = ceil(r_m), capped at 64.
   * Eq. 6/7: anchor s_i = S ln(X_i / X_m) / ln(X_0 / X_m), so s_m = 0 and
     s_0 = S; r equals r_i at iteration s_i and 1/r^2 is linear in k between
     consecutive anchors (Sec. 4.2, last paragraph).
@@ -35,6 +39,9 @@ import math
 from fractions import Fraction
 
 import numpy as np
+
+
+MAX_LEVELS = 64  # cap on the number of levels m (reading: m = ceil(r_m), at most 64)
 
 
 def spectrum_mean(images: np.ndarray) -> np.ndarray:
@@ -61,10 +68,10 @@ def crop_sum(Mbar: np.ndarray, h: int, w: int) -> float:
 
 
 def significance(Mbar: np.ndarray, r) -> float:
-    """X(F_r) of Eq. 2 for the view-mean magnitude spectrum."""
+    """X(F_r) of Eq. 2 for the view-mean magnitude spectrum (pixel-normalised DFT)."""
     H, W = Mbar.shape
     h, w = crop_size(H, W, r)
-    return crop_sum(Mbar, h, w) / float(r) ** 2
+    return crop_sum(Mbar, h, w) / float(H * W)
 
 
 def _breakpoints(H: int, W: int) -> list[Fraction]:
@@ -75,16 +82,16 @@ def _breakpoints(H: int, W: int) -> list[Fraction]:
 
 def solve_r(Mbar: np.ndarray, target: float) -> float:
     """inf{r >= 1 : X(r) <= target}.  On each interval (lo, hi] between
-    consecutive breakpoints the crop is that of hi and X(r) = c / r^2."""
+    consecutive breakpoints the crop is that of hi, so X is constant there and
+    the infimum is the left end lo of the first interval where X <= target."""
     H, W = Mbar.shape
     if significance(Mbar, 1) <= target:
         return 1.0
     lo = Fraction(1)
     for hi in _breakpoints(H, W):
         h, w = crop_size(H, W, hi)
-        c = crop_sum(Mbar, h, w)
-        if c / float(hi) ** 2 <= target:
-            return max(float(lo), math.sqrt(c / target))
+        if crop_sum(Mbar, h, w) / float(H * W) <= target:
+            return float(lo)
         lo = hi
     return float(lo)  # beyond the last breakpoint the crop is empty
 
@@ -99,7 +106,7 @@ class ResolutionSchedule:
         self.Xm = self.X0 / a
         self.r_m = solve_r(Mbar, self.Xm)
         self.m = int(math.ceil(self.r_m)) if m is None else int(m)
-        self.m = max(self.m, 1)
+        self.m = min(max(self.m, 1), MAX_LEVELS)
         self.X = [self.X0 + (i / self.m) * (self.Xm - self.X0) for i in range(self.m + 1)]
         self.r = [1.0] + [solve_r(Mbar, x) for x in self.X[1:]]
         den = math.log(self.X0 / self.Xm)
@@ -165,4 +172,4 @@ def area_downsample(img: np.ndarray, h: int, w: int) -> np.ndarray:
                     Wm[i, j] = float(ov / (b - a))
         return Wm
     Wy, Wx = weights(H, h), weights(W, w)
-    return np.einsum("ih,chw,jw->cij", Wy, img, Wx)
+    return np.stack([Wy @ img[c] @ Wx.T for c in range(C)])

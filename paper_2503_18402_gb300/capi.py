@@ -24,7 +24,10 @@ DG_OK, DG_ERR_ARG, DG_ERR_CAPACITY, DG_ERR_TIMEOUT, DG_ERR_CUDA = 0, -1, -2, -3,
 
 EXPORTS = ("dg_last_error", "dg_abi_version", "dg_kernel_launches", "dg_project", "dg_bin_workspace_size", "dg_bin_count",
            "dg_bin_sort", "dg_render_fwd", "dg_render_bwd", "dg_project_bwd", "dg_loss_workspace_size",
-           "dg_loss_l1", "dg_loss_l1_noalloc", "dg_adam_step")
+           "dg_loss_l1", "dg_loss_l1_noalloc", "dg_adam_step", "dg_spectrum_workspace_size",
+           "dg_spectrum_accumulate", "dg_spectrum_finalize", "dg_downsample_area", "dg_schedule_init",
+           "dg_schedule_step", "dg_schedule_densify", "dg_densify_stats", "dg_densify_workspace_size",
+           "dg_densify_mark", "dg_densify_apply", "dg_mse", "dg_opacity_reset")
 L1_NOALLOC_MAX_N = 1024 * 256 * 1024
 
 
@@ -42,7 +45,44 @@ class Camera(ctypes.Structure):
 
 class RasterOpts(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("near_plane", ctypes.c_float),
-                ("eps2d", ctypes.c_float), ("bg", ctypes.c_float * 3)]
+                ("eps2d", ctypes.c_float), ("bg", ctypes.c_float * 3), ("pixels_per_thread", ctypes.c_int32)]
+
+
+SCHED_MAX_LEVELS = 64
+
+
+class SchedParams(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_int64), ("a", ctypes.c_double), ("m", ctypes.c_int32),
+                ("gamma", ctypes.c_double), ("eta", ctypes.c_double), ("P_init", ctypes.c_double),
+                ("P_cap", ctypes.c_double), ("lr_pos_init", ctypes.c_double), ("lr_pos_final", ctypes.c_double)]
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("p", SchedParams), ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("m", ctypes.c_int32),
+                ("X0", ctypes.c_double), ("Xm", ctypes.c_double), ("r_m", ctypes.c_double),
+                ("X", ctypes.c_double * (SCHED_MAX_LEVELS + 1)), ("r", ctypes.c_double * (SCHED_MAX_LEVELS + 1)),
+                ("s", ctypes.c_double * (SCHED_MAX_LEVELS + 1)), ("k_full", ctypes.c_int64), ("P_fin", ctypes.c_double)]
+
+
+class SchedOut(ctypes.Structure):
+    _fields_ = [("r_cont", ctypes.c_double), ("r_mod", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("width", ctypes.c_int32), ("lr_pos", ctypes.c_double), ("P_target", ctypes.c_double)]
+
+
+class DensifyOpts(ctypes.Structure):
+    _fields_ = [("grad_thresh", ctypes.c_float), ("min_opacity", ctypes.c_float), ("percent_dense", ctypes.c_float),
+                ("extent", ctypes.c_float), ("max_screen_radius", ctypes.c_float), ("max_world_scale", ctypes.c_float)]
+
+
+def densify_opts(grad_thresh=0.0002, min_opacity=0.005, percent_dense=0.01, extent=1.0, max_screen_radius=0.0,
+                 max_world_scale=0.0) -> DensifyOpts:
+    return DensifyOpts(grad_thresh, min_opacity, percent_dense, extent, max_screen_radius, max_world_scale)
+
+
+def sched_params(S, a=4.0, m=0, gamma=0.98, eta=1.0, P_init=1e5, P_cap=3e6, lr_pos_init=1.6e-4,
+                 lr_pos_final=1.6e-6) -> SchedParams:
+    return SchedParams(int(S), float(a), int(m), float(gamma), float(eta), float(P_init), float(P_cap),
+                       float(lr_pos_init), float(lr_pos_final))
 
 
 def camera(viewmat, fx, fy, cx, cy, width, height) -> Camera:
@@ -55,10 +95,12 @@ def camera(viewmat, fx, fy, cx, cy, width, height) -> Camera:
     return c
 
 
-def raster_opts(tile=16, sh_degree=3, near_plane=0.2, eps2d=0.3, bg=(0.0, 0.0, 0.0)) -> RasterOpts:
+def raster_opts(tile=16, sh_degree=3, near_plane=0.2, eps2d=0.3, bg=(0.0, 0.0, 0.0),
+                pixels_per_thread=0) -> RasterOpts:
     o = RasterOpts()
     o.tile, o.sh_degree, o.near_plane, o.eps2d = int(tile), int(sh_degree), float(near_plane), float(eps2d)
     o.bg[:] = [float(b) for b in bg]
+    o.pixels_per_thread = int(pixels_per_thread)
     return o
 
 
@@ -79,13 +121,26 @@ _SIGS = {
     "dg_bin_workspace_size": ([_I64, _I64, _I32], _SZ),
     "dg_bin_count": ([_P, _P, _I64, _P, _SZ, _I64, _I32, _P, _P], _ST),
     "dg_bin_sort": ([_P, _P, _I64, _CAM, _I32, _P, _SZ, _I64, _P, _P, _P, _P], _ST),
-    "dg_render_fwd": ([_P, _P, _P, _CAM, _OPT, _P, _P, _P, _P, _P], _ST),
+    "dg_render_fwd": ([_P, _P, _P, _CAM, _OPT, _P, _P, _P, _P, _P, _P], _ST),
     "dg_render_bwd": ([_P, _P, _P, _CAM, _OPT, _P, _P, _P, _I64, _P, _P], _ST),
     "dg_project_bwd": ([_P, _I64, _I64, _CAM, _OPT, _P, _P, _P, _P, _P], _ST),
     "dg_loss_workspace_size": ([_I64], _SZ),
     "dg_loss_l1": ([_P, _P, _I64, _P, _P, _P, _SZ, _P], _ST),
     "dg_loss_l1_noalloc": ([_P, _P, _I64, _P, _P, _P], _ST),
     "dg_adam_step": ([_P, _P, _P, _P, _I64, _I64, _P, _F, _F, _F, _I64, _P], _ST),
+    "dg_spectrum_workspace_size": ([_I32, _I32], _SZ),
+    "dg_spectrum_accumulate": ([_P, _I32, _I32, _P, _P, _SZ, _P], _ST),
+    "dg_spectrum_finalize": ([_P, _I32, _I32, _I32, _P, _P, _P], _ST),
+    "dg_downsample_area": ([_P, _I32, _I32, _I32, _P, _I32, _I32, _P], _ST),
+    "dg_mse": ([_P, _P, _I64, _P, _P, _SZ, _P], _ST),
+    "dg_opacity_reset": ([_P, _P, _P, _I64, _I64, _F, _P], _ST),
+    "dg_densify_stats": ([_P, _P, _I64, _I32, _I32, _P, _P, _P, _P], _ST),
+    "dg_densify_workspace_size": ([_I64], _SZ),
+    "dg_densify_mark": ([_P, _I64, _I64, _P, _P, _P, ctypes.POINTER(DensifyOpts), _P, _SZ, _P, _P], _ST),
+    "dg_densify_apply": ([_P, _P, _P, _I64, _I64, _I64, _I64, _P, _P, _SZ, _P, _P, _P, _I64, _P, _P], _ST),
+    "dg_schedule_init": ([_P, _I32, _I32, ctypes.POINTER(SchedParams), ctypes.POINTER(Schedule)], _ST),
+    "dg_schedule_step": ([ctypes.POINTER(Schedule), _I64, ctypes.POINTER(SchedOut)], _ST),
+    "dg_schedule_densify": ([ctypes.POINTER(Schedule), _I64, _I64, ctypes.POINTER(SchedOut)], _ST),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -149,9 +204,9 @@ def dg_bin_sort(feat, radius, P, cam, tile, ws, ws_bytes, M_cap, gid, ranges, st
                             _a(gid), _a(ranges), _a(status), _s(stream)))
 
 
-def dg_render_fwd(feat, gid, ranges, cam, opts, img, T_final, last, examined, stream=None):
+def dg_render_fwd(feat, gid, ranges, cam, opts, img, T_final, last, examined, blended=None, stream=None):
     _check(_lib.dg_render_fwd(_a(feat), _a(gid), _a(ranges), ctypes.byref(cam), ctypes.byref(opts), _a(img),
-                              _a(T_final), _a(last), _a(examined), _s(stream)))
+                              _a(T_final), _a(last), _a(examined), _a(blended), _s(stream)))
 
 
 def dg_render_bwd(feat, gid, ranges, cam, opts, T_final, last, dL_dimg, P, grad2d, stream=None):
@@ -183,3 +238,70 @@ def dg_adam_step(params, grads, m, v, stride, P, lr, beta1, beta2, eps, step, st
     _check(_lib.dg_adam_step(_a(params), _a(grads), _a(m), _a(v), stride, P,
                              ctypes.cast(lr_arr, ctypes.c_void_p), beta1, beta2, eps, step, _s(stream)))
 
+
+def dg_spectrum_workspace_size(H, W) -> int:
+    return _lib.dg_spectrum_workspace_size(H, W)
+
+
+def dg_spectrum_accumulate(view, H, W, acc, ws, ws_bytes, stream=None):
+    _check(_lib.dg_spectrum_accumulate(_a(view), H, W, _a(acc), _a(ws), ws_bytes, _s(stream)))
+
+
+def dg_spectrum_finalize(acc, n_views, H, W, shifted, sat, stream=None):
+    _check(_lib.dg_spectrum_finalize(_a(acc), n_views, H, W, _a(shifted), _a(sat), _s(stream)))
+
+
+def dg_downsample_area(src, C, H, W, dst, h, w, stream=None):
+    _check(_lib.dg_downsample_area(_a(src), C, H, W, _a(dst), h, w, _s(stream)))
+
+
+def dg_schedule_init(sat_host, H, W, params: SchedParams) -> Schedule:
+    """sat_host: host float64 array (H+1, W+1), C-contiguous (numpy)."""
+    import numpy as np
+    sat = np.ascontiguousarray(sat_host, dtype=np.float64)
+    assert sat.shape == (H + 1, W + 1)
+    out = Schedule()
+    _check(_lib.dg_schedule_init(sat.ctypes.data_as(ctypes.c_void_p), H, W, ctypes.byref(params),
+                                 ctypes.byref(out)))
+    return out
+
+
+def dg_schedule_step(sched: Schedule, it) -> SchedOut:
+    out = SchedOut()
+    _check(_lib.dg_schedule_step(ctypes.byref(sched), int(it), ctypes.byref(out)))
+    return out
+
+
+def dg_schedule_densify(sched: Schedule, it, P_add) -> SchedOut:
+    out = SchedOut()
+    _check(_lib.dg_schedule_densify(ctypes.byref(sched), int(it), int(P_add), ctypes.byref(out)))
+    return out
+
+
+def dg_densify_stats(grad2d, radius, P, W, H, grad_accum, denom, max_radius, stream=None):
+    _check(_lib.dg_densify_stats(_a(grad2d), _a(radius), P, W, H, _a(grad_accum), _a(denom), _a(max_radius),
+                                 _s(stream)))
+
+
+def dg_densify_workspace_size(P) -> int:
+    return _lib.dg_densify_workspace_size(P)
+
+
+def dg_densify_mark(params, stride, P, grad_accum, denom, max_radius, opts: DensifyOpts, ws, ws_bytes, counts,
+                    stream=None):
+    _check(_lib.dg_densify_mark(_a(params), stride, P, _a(grad_accum), _a(denom), _a(max_radius),
+                                ctypes.byref(opts), _a(ws), ws_bytes, _a(counts), _s(stream)))
+
+
+def dg_densify_apply(params, m, v, stride, P, n_cand, budget, noise, ws, ws_bytes, dst_params, dst_m, dst_v,
+                     dst_stride, P_out, stream=None):
+    _check(_lib.dg_densify_apply(_a(params), _a(m), _a(v), stride, P, n_cand, budget, _a(noise), _a(ws), ws_bytes,
+                                 _a(dst_params), _a(dst_m), _a(dst_v), dst_stride, _a(P_out), _s(stream)))
+
+
+def dg_mse(a, b, n, mse, ws, ws_bytes, stream=None):
+    _check(_lib.dg_mse(_a(a), _a(b), n, _a(mse), _a(ws), ws_bytes, _s(stream)))
+
+
+def dg_opacity_reset(params, m, v, stride, P, max_opacity, stream=None):
+    _check(_lib.dg_opacity_reset(_a(params), _a(m), _a(v), stride, P, max_opacity, _s(stream)))

@@ -49,6 +49,40 @@ __global__ void k_l1_final(const float* __restrict__ partial, int nb, float inv_
     }
 }
 
+// Sum of squared differences, per-block partials (deterministic final sum).
+__global__ void __launch_bounds__(LOSS_THREADS)
+k_sqdiff(const float* __restrict__ a, const float* __restrict__ b, long long n, float* __restrict__ partial)
+{
+    __shared__ float sm[LOSS_THREADS / 32];
+    float acc = 0.f;
+    for (long long i = (long long)blockIdx.x * LOSS_THREADS + threadIdx.x; i < n;
+         i += (long long)gridDim.x * LOSS_THREADS) {
+        const float d = a[i] - b[i];
+        acc = fmaf(d, d, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int w = 0; w < LOSS_THREADS / 32; ++w) s += sm[w];
+        partial[blockIdx.x] = s;
+    }
+}
+
+// Opacity reset of the 3DGS backbone: logit <- min(logit, cap); its Adam moments cleared.
+__global__ void k_opacity_reset(float* __restrict__ prm, float* __restrict__ m, float* __restrict__ v,
+                                long long stride, long long P, float cap)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const long long o = 10 * stride + i;
+    prm[o] = fminf(prm[o], cap);
+    m[o] = 0.f;
+    v[o] = 0.f;
+}
+
 struct AdamRow {
     float lr[DG_NPARAM];
 };
@@ -136,4 +170,32 @@ extern "C" dg_status dg_adam_step(float* params, const float* grads, float* m, f
                                                         (float)bc1, (float)sqrt(bc2), eps);
     dg_note_launch();
     return dg_check_launch("adam");
+}
+
+extern "C" dg_status dg_mse(const float* a, const float* b, int64_t n, float* mse, void* ws, size_t ws_bytes,
+                            dg_stream stream)
+{
+    if (n <= 0) { dg_set_error("n must be positive"); return DG_ERR_ARG; }
+    if (!a || !b || !mse || !ws) { dg_set_error("null buffer"); return DG_ERR_ARG; }
+    if (ws_bytes < dg_loss_workspace_size(n)) { dg_set_error("workspace too small"); return DG_ERR_CAPACITY; }
+    long long nb = (n + dg::LOSS_THREADS - 1) / dg::LOSS_THREADS;
+    if (nb > dg::LOSS_BLOCKS_MAX) nb = dg::LOSS_BLOCKS_MAX;
+    cudaStream_t s = (cudaStream_t)stream;
+    dg::k_sqdiff<<<(int)nb, dg::LOSS_THREADS, 0, s>>>(a, b, n, (float*)ws);
+    dg_note_launch();
+    dg::k_l1_final<<<1, 256, 0, s>>>((const float*)ws, (int)nb, (float)(1.0 / (double)n), mse);
+    dg_note_launch();
+    return dg_check_launch("mse");
+}
+
+extern "C" dg_status dg_opacity_reset(float* params, float* m, float* v, int64_t stride, int64_t P, float max_opacity,
+                                      dg_stream stream)
+{
+    if (P < 0 || stride < P || !(max_opacity > 0.f && max_opacity < 1.f)) { dg_set_error("bad arguments"); return DG_ERR_ARG; }
+    if (P == 0) return DG_OK;
+    if (!params || !m || !v) { dg_set_error("null buffer"); return DG_ERR_ARG; }
+    const float cap = (float)log((double)max_opacity / (1.0 - (double)max_opacity));
+    dg::k_opacity_reset<<<(int)((P + 255) / 256), 256, 0, (cudaStream_t)stream>>>(params, m, v, stride, P, cap);
+    dg_note_launch();
+    return dg_check_launch("opacity_reset");
 }

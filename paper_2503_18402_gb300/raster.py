@@ -36,9 +36,13 @@ class Frame:
 class Rasterizer:
     """Reusable buffers for rendering P Gaussians into one view at a time."""
 
-    def __init__(self, device="cuda", opts: capi.RasterOpts | None = None, pair_headroom: float = 1.25):
+    def __init__(self, device="cuda", opts: capi.RasterOpts | None = None, pair_headroom: float = 1.25,
+                 ppt_fwd: int | None = None, ppt_bwd: int | None = None):
         self.device = torch.device(device)
         self.opts = opts if opts is not None else capi.raster_opts()
+        # launch shape of each render pass (pixels per thread); None keeps opts'
+        self.opts_fwd = self._with_ppt(self.opts, ppt_fwd)
+        self.opts_bwd = self._with_ppt(self.opts, ppt_bwd)
         self.headroom = pair_headroom
         self.P_cap = -1
         self.M_cap = 0
@@ -46,6 +50,13 @@ class Rasterizer:
         self.ws = None
         self.examined = None
         self.mark = None  # optional callback(stage_name) after each stage, for event timing
+
+    @staticmethod
+    def _with_ppt(opts, ppt):
+        o = capi.RasterOpts.from_buffer_copy(opts)
+        if ppt is not None:
+            o.pixels_per_thread = int(ppt)
+        return o
 
     def _mark(self, name):
         if self.mark is not None:
@@ -114,11 +125,13 @@ class Rasterizer:
         img = torch.empty((3, H, W), dtype=torch.float32, device=self.device)
         T = torch.empty((H, W), dtype=torch.float32, device=self.device)
         last = torch.empty((H, W), dtype=torch.int32, device=self.device)
-        ex = None
+        ex = bl = None
         if examined:
             ex = torch.empty((H, W), dtype=torch.int32, device=self.device)
+            bl = torch.empty((H, W), dtype=torch.int32, device=self.device)
             self.examined = ex
-        capi.dg_render_fwd(self.feat, self.gid, self.ranges, cam, self.opts, img, T, last, ex, stream)
+            self.blended = bl
+        capi.dg_render_fwd(self.feat, self.gid, self.ranges, cam, self.opts_fwd, img, T, last, ex, bl, stream)
         self._mark("render_fwd")
         return Frame(P=P, cam=cam, img=img, T=T, last=last, M=M)
 
@@ -127,7 +140,7 @@ class Rasterizer:
         """Writes dL/dparams of the frame into the planar ``grads`` (same stride as params)."""
         stream = stream or torch.cuda.current_stream(self.device)
         assert dL_dimg.is_contiguous() and dL_dimg.dtype == torch.float32
-        capi.dg_render_bwd(self.feat, self.gid, self.ranges, fr.cam, self.opts, fr.T, fr.last, dL_dimg, fr.P,
+        capi.dg_render_bwd(self.feat, self.gid, self.ranges, fr.cam, self.opts_bwd, fr.T, fr.last, dL_dimg, fr.P,
                            self.grad2d, stream)
         self._mark("render_bwd")
         capi.dg_project_bwd(params, params.stride(0), fr.P, fr.cam, self.opts, self.radius, self.clamp,

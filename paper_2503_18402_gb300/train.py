@@ -1,0 +1,289 @@
+"""End-to-end optimisation: plain full-resolution 3DGS training or DashGaussian's
+scheduled training (resolution schedule + resolution-synced primitive budget),
+with every step of every iteration in the CUDA library.
+
+Per iteration k (Sec. 4; supplementary "Learning Rate", "Densification"):
+  schedule step -> render size (H/r, W/r), position learning rate, P target;
+  project -> bin -> render fwd -> L1 -> render bwd -> project bwd ->
+  densification statistics -> Adam;
+  every `densify_every` iterations in [densify_from, densify_until]: prune,
+  Eq. 5 budget update with P_add = candidate count, Eq. 4 target, top-k
+  clone/split (plain arm: every candidate, the 3DGS backbone);
+  every `opacity_reset_every` iterations: opacity reset (3DGS backbone).
+The plain arm renders every iteration at full resolution with the position
+learning rate decaying from iteration 0.
+
+Python here only orders the library calls and owns the device buffers
+(PyTorch allocations); it computes nothing of the method.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+from dataclasses import asdict, dataclass
+
+import numpy as np
+import torch
+
+from . import capi
+from .raster import Rasterizer, make_camera
+from .schedule import spectrum_table
+
+
+@dataclass
+class TrainConfig:
+    iters: int = 30000
+    scheduled: bool = True
+    densify_from: int = 500
+    densify_until: int = 15000
+    densify_every: int = 100
+    opacity_reset_every: int = 3000
+    grad_thresh: float = 2e-4
+    min_opacity: float = 0.005
+    percent_dense: float = 0.01
+    extent: float = 5.5
+    P_cap: int = 3_000_000
+    a: float = 4.0
+    gamma: float = 0.98
+    eta: float = 1.0
+    lr_pos_init: float = 1.6e-4
+    lr_pos_final: float = 1.6e-6
+    lr_dc: float = 0.0025
+    lr_rest: float = 0.0025 / 20
+    lr_opacity: float = 0.025
+    lr_scale: float = 0.005
+    lr_rot: float = 0.001
+    seed: int = 0
+
+
+class Trainer:
+    def __init__(self, cfg: TrainConfig, init: np.ndarray, train_views, train_imgs, device="cuda"):
+        """init: (P0, 59) parameters; train_views: camera dicts (full
+        resolution); train_imgs: list of (3, H, W) float32 device tensors."""
+        self.cfg = cfg
+        self.dev = torch.device(device)
+        self.views = train_views
+        self.imgs = train_imgs
+        self.H, self.W = train_imgs[0].shape[1], train_imgs[0].shape[2]
+        cap = max(cfg.P_cap, init.shape[0]) + 1024
+        self.cap = cap
+        f32 = dict(dtype=torch.float32, device=self.dev)
+        self.buf = [dict(p=torch.zeros((59, cap), **f32), m=torch.zeros((59, cap), **f32),
+                         v=torch.zeros((59, cap), **f32)) for _ in range(2)]
+        self.cur = 0
+        self.P = init.shape[0]
+        self.buf[0]["p"][:, : self.P] = torch.from_numpy(np.ascontiguousarray(init.T.astype(np.float32))).to(self.dev)
+        self.grads = torch.zeros((59, cap), **f32)
+        self.acc = torch.zeros(cap, **f32)
+        self.den = torch.zeros(cap, **f32)
+        self.maxr = torch.zeros(cap, **f32)
+        self.rz = Rasterizer(self.dev, capi.raster_opts())
+        n_full = 3 * self.H * self.W
+        self.dL = torch.empty(n_full, **f32)
+        self.loss = torch.zeros(1, **f32)
+        self.lws = torch.empty(capi.dg_loss_workspace_size(n_full), dtype=torch.uint8, device=self.dev)
+        self.dws = None
+        self.counts = torch.zeros(2, dtype=torch.int64, device=self.dev)
+        self.P_out = torch.zeros(1, dtype=torch.int64, device=self.dev)
+        self.gen = torch.Generator(device=self.dev)
+        self.gen.manual_seed(cfg.seed)
+        self.order_rng = np.random.default_rng(cfg.seed)
+        self.order = []
+        self.gt_cache = {}
+        self.stream = torch.cuda.current_stream(self.dev)
+        self.sched = None
+        self.history = []
+        self.init_schedule_s = 0.0
+
+    # ---------------------------------------------------------------- schedule
+    def init_schedule(self):
+        t0 = time.perf_counter()
+        cfg = self.cfg
+        _, sat = spectrum_table(self.imgs, self.dev)
+        p = capi.sched_params(cfg.iters, a=cfg.a, gamma=cfg.gamma, eta=cfg.eta, P_init=float(self.P),
+                              P_cap=float(cfg.P_cap), lr_pos_init=cfg.lr_pos_init * cfg.extent,
+                              lr_pos_final=cfg.lr_pos_final * cfg.extent)
+        self.sched = capi.dg_schedule_init(sat, self.H, self.W, p)
+        torch.cuda.synchronize()
+        self.init_schedule_s = time.perf_counter() - t0
+
+    def _plan(self, k):
+        cfg = self.cfg
+        if self.sched is not None:
+            o = capi.dg_schedule_step(self.sched, k)
+            return o.r_mod, o.height, o.width, o.lr_pos
+        t = min(1.0, k / cfg.iters)
+        lr = math.exp((1 - t) * math.log(cfg.lr_pos_init * cfg.extent) + t * math.log(cfg.lr_pos_final * cfg.extent))
+        return 1, self.H, self.W, lr
+
+    def _target(self, j, r, h, w):
+        if r == 1:
+            return self.imgs[j]
+        key = (j, r)
+        t = self.gt_cache.get(key)
+        if t is None:
+            t = torch.empty((3, h, w), dtype=torch.float32, device=self.dev)
+            capi.dg_downsample_area(self.imgs[j], 3, self.H, self.W, t, h, w, self.stream)
+            self.gt_cache[key] = t
+        return t
+
+    def _camera(self, j, h, w):
+        v = self.views[j]
+        fx, fy, cx, cy = v["intr"]
+        sx, sy = w / self.W, h / self.H
+        return make_camera(np.asarray(v["viewmat"], np.float32).reshape(-1), (fx * sx, fy * sy, cx * sx, cy * sy), w, h)
+
+    def _next_view(self):
+        if not self.order:
+            self.order = list(self.order_rng.permutation(len(self.views)))
+        return int(self.order.pop())
+
+    # ---------------------------------------------------------------- step
+    def step(self, k):
+        cfg = self.cfg
+        b = self.buf[self.cur]
+        P = self.P
+        r, h, w, lr_pos = self._plan(k)
+        j = self._next_view()
+        cam = self._camera(j, h, w)
+        params = b["p"][:, :P]
+        fr = self.rz.forward(params, P, cam, self.stream)
+        n = 3 * h * w
+        capi.dg_loss_l1(fr.img, self._target(j, r, h, w), n, self.dL, self.loss, self.lws, self.lws.numel(), self.stream)
+        self.rz.backward(params, fr, self.dL[:n].view(3, h, w), self.grads[:, :P], self.stream)
+        if k < cfg.densify_until:
+            capi.dg_densify_stats(self.rz.grad2d, self.rz.radius, P, w, h, self.acc, self.den, self.maxr, self.stream)
+        lr = [lr_pos] * 3 + [cfg.lr_scale] * 3 + [cfg.lr_rot] * 4 + [cfg.lr_opacity] + [cfg.lr_dc] * 3 + \
+             [cfg.lr_rest] * 45
+        capi.dg_adam_step(b["p"], self.grads, b["m"], b["v"], self.cap, P, lr, 0.9, 0.999, 1e-15, k + 1, self.stream)
+        kk = k + 1
+        if cfg.densify_from <= kk <= cfg.densify_until and kk % cfg.densify_every == 0:
+            self.densify(kk)
+        if kk % cfg.opacity_reset_every == 0 and kk <= cfg.densify_until:
+            b = self.buf[self.cur]
+            capi.dg_opacity_reset(b["p"], b["m"], b["v"], self.cap, self.P, 0.01, self.stream)
+        return r, fr.M
+
+    def densify(self, k):
+        cfg = self.cfg
+        P = self.P
+        b = self.buf[self.cur]
+        dst = self.buf[1 - self.cur]
+        need = capi.dg_densify_workspace_size(P)
+        if self.dws is None or self.dws.numel() < need:
+            self.dws = torch.empty(int(need * 1.2) + 1024, dtype=torch.uint8, device=self.dev)
+        big = k > cfg.opacity_reset_every
+        opts = capi.densify_opts(cfg.grad_thresh, cfg.min_opacity, cfg.percent_dense, cfg.extent,
+                                 20.0 if big else 0.0, 0.1 * cfg.extent if big else 0.0)
+        capi.dg_densify_mark(b["p"], self.cap, P, self.acc, self.den, self.maxr, opts, self.dws, self.dws.numel(),
+                             self.counts, self.stream)
+        n_keep, n_cand = (int(x) for x in self.counts.cpu())
+        if self.sched is not None:
+            o = capi.dg_schedule_densify(self.sched, k, n_cand)
+            budget = max(0, int(o.P_target) - n_keep)
+        else:
+            budget = n_cand
+        budget = max(0, min(budget, cfg.P_cap - n_keep))
+        n_sel = min(budget, n_cand)
+        noise = torch.randn((max(n_sel, 1), 2, 3), generator=self.gen, device=self.dev)
+        capi.dg_densify_apply(b["p"], b["m"], b["v"], self.cap, P, n_cand, budget, noise, self.dws, self.dws.numel(),
+                              dst["p"], dst["m"], dst["v"], self.cap, self.P_out, self.stream)
+        self.P = int(self.P_out.item())
+        self.cur = 1 - self.cur
+        self.acc.zero_(); self.den.zero_(); self.maxr.zero_()
+        self.history.append(dict(iter=k, P=self.P, n_keep=n_keep, n_cand=n_cand, budget=budget))
+
+    # ---------------------------------------------------------------- eval
+    def psnr(self, views, imgs):
+        b = self.buf[self.cur]
+        out = torch.zeros(1, dtype=torch.float32, device=self.dev)
+        vals = []
+        for v, gt in zip(views, imgs):
+            cam = make_camera(np.asarray(v["viewmat"], np.float32).reshape(-1), v["intr"], self.W, self.H)
+            fr = self.rz.forward(b["p"][:, : self.P], self.P, cam, self.stream)
+            capi.dg_mse(fr.img, gt, 3 * self.H * self.W, out, self.lws, self.lws.numel(), self.stream)
+            vals.append(-10.0 * math.log10(max(float(out.item()), 1e-12)))
+        return float(np.mean(vals))
+
+    def run(self, log_every=0):
+        cfg = self.cfg
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if cfg.scheduled:
+            self.init_schedule()
+        res_hist = {}
+        for k in range(cfg.iters):
+            r, M = self.step(k)
+            res_hist[r] = res_hist.get(r, 0) + 1
+            if log_every and (k + 1) % log_every == 0:
+                torch.cuda.synchronize()
+                print(json.dumps(dict(iter=k + 1, P=self.P, r=r, loss=float(self.loss.item()),
+                                      s=round(time.perf_counter() - t0, 2))), flush=True)
+        torch.cuda.synchronize()
+        return dict(seconds=time.perf_counter() - t0, schedule_init_s=self.init_schedule_s, P_final=self.P,
+                    iters_per_factor={str(k): v for k, v in sorted(res_hist.items())})
+
+
+def make_dataset(n_gt, n_views, W, H, device, seed=1001):
+    """GT scene, cameras and GT renders; every 8th view held out."""
+    from . import synth
+    gt = synth.textured_scene(n_gt, seed)
+    cams = synth.ring_cameras(n_views, W, H, 5.0, seed + 1000)
+    rz = Rasterizer(device, capi.raster_opts())
+    gtp = torch.from_numpy(np.ascontiguousarray(gt.T)).to(device)
+    imgs = []
+    for v in cams:
+        cam = make_camera(np.asarray(v["viewmat"], np.float32).reshape(-1), v["intr"], W, H)
+        imgs.append(rz.forward(gtp, gt.shape[0], cam).img.clone())
+    del gtp
+    test = [i for i in range(n_views) if i % 8 == 0]
+    train = [i for i in range(n_views) if i % 8 != 0]
+    return gt, cams, imgs, train, test
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--arm", choices=["plain", "scheduled", "both"], default="both")
+    ap.add_argument("--iters", type=int, default=30000)
+    ap.add_argument("--n-gt", type=int, default=2_000_000)
+    ap.add_argument("--n-init", type=int, default=100_000)
+    ap.add_argument("--views", type=int, default=160)
+    ap.add_argument("--width", type=int, default=1237)
+    ap.add_argument("--height", type=int, default=822)
+    ap.add_argument("--p-cap", type=int, default=3_000_000)
+    ap.add_argument("--log-every", type=int, default=0)
+    args = ap.parse_args(argv)
+    from . import synth
+    dev = torch.device("cuda")
+    gt, cams, imgs, train, test = make_dataset(args.n_gt, args.views, args.width, args.height, dev)
+    init = synth.perturb(gt, 3001, n_keep=args.n_init)
+    arms = ["plain", "scheduled"] if args.arm == "both" else [args.arm]
+    results = {}
+    for arm in arms:
+        cfg = TrainConfig(iters=args.iters, scheduled=(arm == "scheduled"), P_cap=args.p_cap)
+        if args.iters < 30000:  # compress the backbone's iteration windows proportionally
+            s = args.iters / 30000
+            cfg.densify_from = max(1, int(500 * s)); cfg.densify_until = int(15000 * s)
+            cfg.densify_every = max(1, int(100 * s)); cfg.opacity_reset_every = max(1, int(3000 * s))
+        tr = Trainer(cfg, init, [cams[i] for i in train], [imgs[i] for i in train], dev)
+        res = tr.run(log_every=args.log_every)
+        res["psnr_test"] = tr.psnr([cams[i] for i in test], [imgs[i] for i in test])
+        res["densify_last"] = tr.history[-1] if tr.history else None
+        if tr.sched is not None:
+            s = tr.sched
+            res["schedule"] = dict(r_m=s.r_m, m=s.m, k_full=s.k_full, P_fin=s.P_fin,
+                                   anchors=[(s.s[i], s.r[i]) for i in range(s.m + 1)])
+        results[arm] = res
+        print(json.dumps({arm: res}), flush=True)
+        del tr
+        torch.cuda.empty_cache()
+    print(json.dumps(dict(config=vars(args), results=results)), flush=True)
+    return results
+
+
+if __name__ == "__main__":
+    sys.exit(0 if main() else 1)

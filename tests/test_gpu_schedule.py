@@ -1,0 +1,60 @@
+"""GPU parts of the schedule vs the FP64 oracle: the FP64-accumulated view-mean
+DFT magnitude spectrum (Eq. 2) with its summed-area table, the schedule built
+from it (Sec. 4.2, Eq. 7), and the area downsampling of the ground truth."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from oracle import schedule as sch  # noqa: E402
+from paper_2503_18402_gb300 import capi  # noqa: E402
+from paper_2503_18402_gb300 import schedule as gsch  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _views(n, H, W, seed):
+    rng = np.random.default_rng(seed)
+    ky = np.fft.fftfreq(H)[:, None]; kx = np.fft.fftfreq(W)[None, :]
+    amp = 1 / np.maximum(np.hypot(ky, kx), 1 / max(H, W)) ** 1.2
+    v = np.stack([[np.real(np.fft.ifft2(amp * np.exp(2j * math.pi * rng.uniform(size=(H, W)))))
+                   for _ in range(3)] for _ in range(n)])
+    v = (v - v.min()) / (v.max() - v.min())
+    return v.astype(np.float32)
+
+
+@pytest.mark.parametrize("n,H,W", [(3, 64, 96), (2, 67, 131), (2, 205, 309)])
+def test_spectrum_and_table_match_oracle(n, H, W):
+    v = _views(n, H, W, n + H)
+    shifted, sat = gsch.spectrum_table([torch.from_numpy(x).cuda() for x in v])
+    ref = sch.spectrum_mean(v.astype(np.float64))
+    got = shifted.cpu().numpy()
+    # FP32 DFT products, FP64 accumulation: errors are relative to the spectrum's scale
+    scale = ref.max()
+    assert np.abs(got - ref).max() <= 2e-6 * scale
+    ref_sat = np.zeros((H + 1, W + 1)); ref_sat[1:, 1:] = ref.cumsum(0).cumsum(1)
+    assert np.abs(sat - ref_sat).max() <= 2e-6 * ref_sat.max()
+    # schedule from the GPU table equals the oracle's schedule
+    S = 30000
+    s = capi.dg_schedule_init(sat, H, W, capi.sched_params(S))
+    rs = sch.ResolutionSchedule(ref, S)
+    assert s.m == rs.m
+    assert s.r_m == pytest.approx(rs.r_m, rel=1e-4)
+    seq = [capi.dg_schedule_step(s, k).r_mod for k in range(0, S + 1, 50)]
+    ref_seq = [rs.r_mod(k) for k in range(0, S + 1, 50)]
+    assert sum(a != b for a, b in zip(seq, ref_seq)) <= 2  # only at level boundaries
+
+
+@pytest.mark.parametrize("H,W,h,w", [(822, 1237, 205, 309), (822, 1237, 411, 618), (40, 56, 40, 56), (37, 53, 5, 7)])
+def test_area_downsample_matches_oracle(H, W, h, w):
+    rng = np.random.default_rng(H + w)
+    img = rng.uniform(size=(3, H, W)).astype(np.float32)
+    got = gsch.downsample(torch.from_numpy(img).cuda(), h, w).cpu().numpy()
+    ref = sch.area_downsample(img.astype(np.float64), h, w)
+    assert np.abs(got - ref).max() <= 1e-6

@@ -171,6 +171,7 @@ def test_transmittance_product_and_termination():
     assert out["T"][16, 16] == pytest.approx(0.5 ** 13, rel=1e-13)
     assert out["last"][16, 16] == 13
     assert out["examined"][16, 16] == 14
+    assert out["blended"][16, 16] == 13
     # a lighter stack: no termination, T = (1-a)^K
     g = _stack(6, 0.3, cols)
     out = _render(g, cam)

@@ -39,52 +39,62 @@ def test_spectrum_mean_matches_direct_dft():
     np.testing.assert_allclose(sch.spectrum_mean(imgs), shifted, rtol=1e-12)
 
 
-def test_constant_image_gives_r_m_sqrt_a():
-    # all energy at DC: X(r) = |DC| / r^2, so X(r_m) = X(1)/a at r_m = sqrt(a)
+def test_constant_image_keeps_all_significance_at_dc():
+    # all magnitude at DC: X(r) = X(1) while the crop is non-empty, so X(1)/a is
+    # only reached where the crop empties, at r = min(H, W)
     imgs = np.full((1, 3, 32, 48), 0.4)
     Mb = sch.spectrum_mean(imgs)
-    assert sch.significance(Mb, 1) == pytest.approx(3 * 0.4 * 32 * 48, rel=1e-12)
-    for a in (4.0, 9.0, 2.25):
-        assert sch.solve_r(Mb, sch.significance(Mb, 1) / a) == pytest.approx(math.sqrt(a), rel=1e-12)
+    assert sch.significance(Mb, 1) == pytest.approx(3 * 0.4, rel=1e-12)  # pixel-normalised DC
+    for r in (1.7, 5, 20, 31.9, 32):
+        assert sch.significance(Mb, r) == pytest.approx(3 * 0.4, rel=1e-12)
+    assert sch.significance(Mb, 32.5) == 0.0
+    for a in (4.0, 9.0):
+        assert sch.solve_r(Mb, sch.significance(Mb, 1) / a) == 32.0
+
+
+def _cos_X(W, f, c0, A, r):
+    w = math.floor(Fraction(W) / Fraction(r))
+    plus = f <= math.ceil(w / 2) - 1
+    minus = f <= w // 2
+    return 3 * (c0 + 0.5 * A * plus + 0.5 * A * minus)
 
 
 def test_cosine_image_closed_form_and_jump():
     H, W, f, c0, A = 32, 48, 6, 0.5, 0.3
     Mb = sch.spectrum_mean(_cosine_image(H, W, f, c0, A))
-    unit = 3 * H * W
-
-    def X_closed(r):
-        w = math.floor(W / r)
-        plus = f <= math.ceil(w / 2) - 1
-        minus = f <= w // 2
-        return unit * (c0 + 0.5 * A * plus + 0.5 * A * minus) / float(r) ** 2
     for r in (1, 1.5, 2, 3.5, Fraction(48, 13), 3.8, 4, 4.2, 6):
-        assert sch.significance(Mb, r) == pytest.approx(X_closed(r), rel=1e-10)
+        assert sch.significance(Mb, r) == pytest.approx(_cos_X(W, f, c0, A, r), rel=1e-10)
     X0 = sch.significance(Mb, 1)
-    assert sch.solve_r(Mb, X0 / 4) == pytest.approx(2.0, rel=1e-10)
-    # a = 20: X never equals X0/20 inside an interval; the infimum is the jump at r = 4
-    assert sch.solve_r(Mb, X0 / 20) == pytest.approx(4.0, rel=1e-12)
+    # X = 0.8, 0.65 (w = 12) or 0.5 (w <= 11), x3: the first level below X0/1.5 is w <= 11, r > 4
+    assert sch.solve_r(Mb, X0 / 1.5) == 4.0
+    # X <= 0.7 x3 first holds for w = 12, i.e. r just above 48/13
+    assert sch.solve_r(Mb, 3 * 0.7) == pytest.approx(48 / 13, rel=1e-15)
+    assert sch.solve_r(Mb, 3 * 0.9) == 1.0
 
 
 def test_eq7_anchors_by_hand():
     H, W, f, c0, A = 32, 48, 6, 0.5, 0.3
     Mb = sch.spectrum_mean(_cosine_image(H, W, f, c0, A))
     S = 30000
-    rs = sch.ResolutionSchedule(Mb, S, a=4.0)
-    assert rs.r_m == pytest.approx(2.0, rel=1e-10)
-    assert rs.m == 2
-    # X_1 = (X0 + X0/4)/2 = 0.625 X0;  s_1 = S ln(0.625/0.25) / ln(4)
-    assert rs.s[0] == pytest.approx(S, rel=1e-12)
-    assert rs.s[1] == pytest.approx(S * math.log(2.5) / math.log(4.0), rel=1e-12)
-    assert rs.s[2] == pytest.approx(0.0, abs=1e-9)
-    # r_1: 0.8 / r^2 = 0.625 * 0.8
-    assert rs.r[1] == pytest.approx(math.sqrt(1 / 0.625), rel=1e-10)
-    # r(k) hits the anchors, 1/r^2 is linear between them
-    assert rs.r_cont(0) == pytest.approx(2.0, rel=1e-10)
-    assert rs.r_cont(rs.s[1]) == pytest.approx(rs.r[1], rel=1e-10)
-    k = 0.5 * rs.s[1]
-    assert 1 / rs.r_cont(k) ** 2 == pytest.approx(0.5 * (1 / 4 + 1 / rs.r[1] ** 2), rel=1e-12)
+    rs = sch.ResolutionSchedule(Mb, S, a=1.5)
+    assert rs.r_m == 4.0 and rs.m == 4
+    # X_i = X0 + (i/4)(X0/1.5 - X0) with X0 = 2.4: 2.4, 2.2, 2.0, 1.8, 1.6
+    np.testing.assert_allclose(rs.X, [2.4, 2.2, 2.0, 1.8, 1.6], rtol=1e-12)
+    # r_i: X <= 2.2 and X <= 2.0 first at w = 12 (X = 1.95): r = 48/13; X <= 1.8 at w = 11: r = 4
+    np.testing.assert_allclose(rs.r, [1.0, 48 / 13, 48 / 13, 4.0, 4.0], rtol=1e-15)
+    # Eq. 7: s_i = S ln(X_i / X_m) / ln(X_0 / X_m)
+    want = [S * math.log(x / 1.6) / math.log(1.5) for x in (2.4, 2.2, 2.0, 1.8, 1.6)]
+    np.testing.assert_allclose(rs.s, want, rtol=1e-12, atol=1e-9)
+    assert rs.s[0] == pytest.approx(S) and rs.s[4] == pytest.approx(0.0, abs=1e-9)
+    # r(k): r_m at k = 0, r_i at s_i, 1/r^2 linear in between
+    assert rs.r_cont(0) == 4.0 and rs.r_mod(0) == 4
+    assert rs.r_cont(rs.s[1]) == pytest.approx(48 / 13, rel=1e-12)
+    k = 0.5 * (rs.s[1] + rs.s[0])
+    assert 1 / rs.r_cont(k) ** 2 == pytest.approx(0.5 * (1 + (13 / 48) ** 2), rel=1e-12)
     assert rs.r_cont(S) == pytest.approx(1.0)
+    # rendering factor sequence: 4, 3 (once r < 4), 2, 1
+    seq = [rs.r_mod(k) for k in range(0, S + 1, 10)]
+    assert seq[0] == 4 and seq[-1] == 1 and sorted(set(seq)) == [1, 2, 3, 4]
 
 
 def test_r_mod_sequence_monotone_and_lr_rule():
