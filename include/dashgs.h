@@ -63,6 +63,7 @@ typedef int32_t dg_status;
 
 #define DG_NPARAM 59
 #define DG_FEAT_FLOATS 12     /* floats per projected record, see dg_project */
+#define DG_MAX_VIEWS 16       /* views per batched call */
 
 typedef void* dg_stream;      /* cudaStream_t */
 
@@ -100,10 +101,20 @@ DG_API int32_t dg_abi_version(void);
 DG_API int64_t dg_kernel_launches(void);
 
 /* ---------------------------------------------------------------------- */
+/* Several views per call.  The projection, binning, render and adjoint calls
+ * take a host array of n_views (1..DG_MAX_VIEWS) cameras.  A "record" is a
+ * (view, Gaussian) pair with index r = v * P + i; per-record arrays are
+ * view-major [n_views][P].  Tiles of all views share one range table: view v's
+ * tiles are ids toff[v] .. toff[v+1]-1 with toff the running sum of
+ * ceil(W_v/B) * ceil(H_v/B).  Per-pixel arrays concatenate the views: images
+ * [v][3][H_v][W_v] from element 3 * poff[v], T/last from poff[v], poff the
+ * running sum of W_v * H_v. */
+
 /* Projection (EWA splatting of Sec. 3, "2D Gaussian splatted to the image
  * plane", and the SH colour of the colour coefficients c_i).
- * In:  params [59][stride] planar float32, P Gaussians, *cam, *opts (host).
- * Out: feat   [P][12] float32, 16-byte aligned, per Gaussian
+ * In:  params [59][stride] planar float32, P Gaussians, cams[n_views], *opts (host).
+ * Out (per record r = v * P + i):
+ *      feat   [P][12] float32, 16-byte aligned, per record
  *              (u, v, A, B | C, o, r, g | b, 0, 0, 0): pixel mean, conic
  *              (A, B, C) = inverse 2D covariance (power = -A dx^2/2 - C dy^2/2
  *              - B dx dy), opacity, colour;
@@ -113,8 +124,8 @@ DG_API int64_t dg_kernel_launches(void);
  *      clamp  [P] uint8, bit c set when colour channel c was clamped at 0.
  * Errors: DG_ERR_ARG for null pointers, P < 0, stride < P, sh_degree
  * outside 0..3, tile < 1, non-positive image size or focal length. */
-DG_API dg_status dg_project(const float* params, int64_t stride, int64_t P, const dg_camera* cam,
-                     const dg_raster_opts* opts, float* feat, float* depth, int32_t* radius,
+DG_API dg_status dg_project(const float* params, int64_t stride, int64_t P, const dg_camera* cams,
+                     int32_t n_views, const dg_raster_opts* opts, float* feat, float* depth, int32_t* radius,
                      int32_t* tiles, uint8_t* clamp, dg_stream stream);
 
 /* ---------------------------------------------------------------------- */
@@ -123,61 +134,68 @@ DG_API dg_status dg_project(const float* params, int64_t stride, int64_t P, cons
  * a view holds one (tile, Gaussian) entry per tile in each Gaussian's rect,
  * ordered by (tile id = ty * TX + tx, depth as float bits, Gaussian index).
  *
- * Bytes of device workspace needed to bin P Gaussians into at most M_cap
- * pairs over n_tiles tiles (host call, no device work). */
-DG_API size_t dg_bin_workspace_size(int64_t P, int64_t M_cap, int32_t n_tiles);
+ * Bytes of device workspace needed to bin P Gaussians in n_views views into
+ * at most M_cap pairs (host call, no device work). */
+DG_API size_t dg_bin_workspace_size(int64_t P, int32_t n_views, int64_t M_cap);
 
-/* Phase 1: orders the visible Gaussians by (depth bits, index) and computes
- * each one's first pair slot.  Writes the total pair count M to *M_out
- * (device int64).  The caller reads M (or checks it against its capacity)
- * before phase 2.  ws/ws_bytes: workspace from dg_bin_workspace_size with
- * the same P; its content carries over to dg_bin_sort. */
-DG_API dg_status dg_bin_count(const float* depth, const int32_t* tiles, int64_t P, void* ws,
-                       size_t ws_bytes, int64_t M_cap, int32_t n_tiles, int64_t* M_out,
-                       dg_stream stream);
+/* Phase 1: orders the visible records by (view, depth bits, index) and
+ * computes each one's first pair slot.  Writes the total pair count M to
+ * *M_out (device int64).  The caller reads M (or checks it against its
+ * capacity) before phase 2.  ws/ws_bytes: workspace from
+ * dg_bin_workspace_size with the same P and n_views; its content carries
+ * over to dg_bin_sort (a workspace laid out for another M_cap is fine as
+ * long as phase 1 ran in it). */
+DG_API dg_status dg_bin_count(const float* depth, const int32_t* tiles, int64_t P, int32_t n_views, void* ws,
+                       size_t ws_bytes, int64_t M_cap, int64_t* M_out, dg_stream stream);
 
-/* Phase 2: emits the pairs in depth order and stably sorts them by tile.
- * Out: gid    [M_cap] uint32, Gaussian index of each sorted pair;
- *      ranges [2 * n_tiles] uint32, [start, end) of each tile's list;
+/* Phase 2: emits the pairs in (view, depth) order and stably sorts them by
+ * global tile id.
+ * Out: gid    [M_cap] uint32, record index v * P + i of each sorted pair;
+ *      ranges [2 * total tiles] uint32, [start, end) of each tile's list;
  *      status (device int32): 0, or DG_ERR_CAPACITY when M > M_cap, in which
  *              case gid is untouched and every range is empty.
- * feat/radius are dg_project's outputs for the same P. */
-DG_API dg_status dg_bin_sort(const float* feat, const int32_t* radius, int64_t P, const dg_camera* cam,
-                      int32_t tile, void* ws, size_t ws_bytes, int64_t M_cap, uint32_t* gid,
+ * feat/radius are dg_project's outputs for the same P and cameras. */
+DG_API dg_status dg_bin_sort(const float* feat, const int32_t* radius, int64_t P, const dg_camera* cams,
+                      int32_t n_views, int32_t tile, void* ws, size_t ws_bytes, int64_t M_cap, uint32_t* gid,
                       uint32_t* ranges, int32_t* status, dg_stream stream);
 
 /* ---------------------------------------------------------------------- */
+/* Render workspace (a work counter of the persistent launch): bytes. */
+DG_API size_t dg_render_workspace_size(void);
+
 /* Forward compositing, Eq. 1: per pixel, front to back over its tile's list,
- * C = sum_i T_i alpha_i c_i + T_N bg.
+ * C = sum_i T_i alpha_i c_i + T_N bg.  One persistent launch covers every
+ * tile of every view (work items taken from a counter in ws).
  * Out: img [3][H][W] float32 (planar RGB), T_final [H][W] float32,
  *      last [H][W] int32 = 1-based list position of the last blended Gaussian
  *      (0 if none), examined [H][W] int32 (nullable) = list entries visited
  *      including the one that stopped compositing, blended [H][W] int32
  *      (nullable) = entries blended into the pixel. */
 DG_API dg_status dg_render_fwd(const float* feat, const uint32_t* gid, const uint32_t* ranges,
-                        const dg_camera* cam, const dg_raster_opts* opts, float* img,
-                        float* T_final, int32_t* last, int32_t* examined, int32_t* blended,
-                        dg_stream stream);
+                        const dg_camera* cams, int32_t n_views, const dg_raster_opts* opts, float* img,
+                        float* T_final, int32_t* last, int32_t* examined, int32_t* blended, void* ws,
+                        size_t ws_bytes, dg_stream stream);
 
 /* Adjoint of Eq. 1 ("fully differentiable", Sec. 3).  Recomputes each
  * pixel's transmittance back to front from T_final and last (no per-pair
  * state), with dC/dc_j = alpha_j T_j and
  * dC/dalpha_j = T_j c_j - S_j / (1 - alpha_j), S_j the colour behind j
  * including T_N bg.
- * In:  dL_dimg [3][H][W] float32.
- * Out: grad2d [P][12] float32, 16-byte aligned, zeroed by this call, then
- *      accumulated: (dL/du, dL/dv, dL/dA, dL/dB | dL/dC, dL/do, dL/dr, dL/dg |
- *      dL/db, 0, 0, 0). */
+ * In:  dL_dimg, laid out like the images.
+ * Out: grad2d [n_records][12] float32 (n_records = n_views * P), 16-byte
+ *      aligned, zeroed by this call, then accumulated per record:
+ *      (dL/du, dL/dv, dL/dA, dL/dB | dL/dC, dL/do, dL/dr, dL/dg | dL/db, 0, 0, 0). */
 DG_API dg_status dg_render_bwd(const float* feat, const uint32_t* gid, const uint32_t* ranges,
-                        const dg_camera* cam, const dg_raster_opts* opts, const float* T_final,
-                        const int32_t* last, const float* dL_dimg, int64_t P, float* grad2d,
-                        dg_stream stream);
+                        const dg_camera* cams, int32_t n_views, const dg_raster_opts* opts, const float* T_final,
+                        const int32_t* last, const float* dL_dimg, int64_t n_records, float* grad2d, void* ws,
+                        size_t ws_bytes, dg_stream stream);
 
-/* Adjoint of dg_project: from grad2d to the gradient of every parameter row.
+/* Adjoint of dg_project: from grad2d (all views) to the gradient of every
+ * parameter row, summed over the views.
  * Out: grads [59][stride] planar float32, overwritten for Gaussians 0..P-1
- *      (zero for culled ones; rows above the SH degree are zero). */
-DG_API dg_status dg_project_bwd(const float* params, int64_t stride, int64_t P, const dg_camera* cam,
-                         const dg_raster_opts* opts, const int32_t* radius, const uint8_t* clamp,
+ *      (zero where culled in every view; rows above the SH degree are zero). */
+DG_API dg_status dg_project_bwd(const float* params, int64_t stride, int64_t P, const dg_camera* cams,
+                         int32_t n_views, const dg_raster_opts* opts, const int32_t* radius, const uint8_t* clamp,
                          const float* grad2d, float* grads, dg_stream stream);
 
 /* ---------------------------------------------------------------------- */
@@ -246,11 +264,13 @@ typedef struct dg_densify_opts {
     float max_world_scale;    /* > 0: also prune when the largest scale exceeds it */
 } dg_densify_opts;
 
-/* After each rendered view: for Gaussians with radius > 0,
- * grad_accum += |(dL/du W/2, dL/dv H/2)| (the NDC-space gradient norm),
- * denom += 1, max_radius = max(max_radius, radius).  All [P] float32. */
-DG_API dg_status dg_densify_stats(const float* grad2d, const int32_t* radius, int64_t P, int32_t W, int32_t H,
-                                  float* grad_accum, float* denom, float* max_radius, dg_stream stream);
+/* After rendering: for each view v and Gaussian with radius[v*P+i] > 0,
+ * grad_accum += |(dL/du W_v/2, dL/dv H_v/2)| (the NDC-space gradient norm),
+ * denom += 1, max_radius = max(max_radius, radius).  grad_accum, denom,
+ * max_radius: [P] float32. */
+DG_API dg_status dg_densify_stats(const float* grad2d, const int32_t* radius, int64_t P, const dg_camera* cams,
+                                  int32_t n_views, float* grad_accum, float* denom, float* max_radius,
+                                  dg_stream stream);
 DG_API size_t dg_densify_workspace_size(int64_t P);
 /* Phase 1: prune/candidate/split flags into ws; counts (device int64[2]) =
  * {N' kept, candidates}.  The caller reads the counts (Eq. 5's P_add is the

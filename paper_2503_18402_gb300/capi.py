@@ -22,8 +22,10 @@ NPARAM = 59
 FEAT_FLOATS = 12
 DG_OK, DG_ERR_ARG, DG_ERR_CAPACITY, DG_ERR_TIMEOUT, DG_ERR_CUDA = 0, -1, -2, -3, -4
 
+MAX_VIEWS = 16
 EXPORTS = ("dg_last_error", "dg_abi_version", "dg_kernel_launches", "dg_project", "dg_bin_workspace_size", "dg_bin_count",
-           "dg_bin_sort", "dg_render_fwd", "dg_render_bwd", "dg_project_bwd", "dg_loss_workspace_size",
+           "dg_bin_sort", "dg_render_workspace_size", "dg_render_fwd", "dg_render_bwd", "dg_project_bwd",
+           "dg_loss_workspace_size",
            "dg_loss_l1", "dg_loss_l1_noalloc", "dg_adam_step", "dg_spectrum_workspace_size",
            "dg_spectrum_accumulate", "dg_spectrum_finalize", "dg_downsample_area", "dg_schedule_init",
            "dg_schedule_step", "dg_schedule_densify", "dg_densify_stats", "dg_densify_workspace_size",
@@ -117,13 +119,14 @@ _SIGS = {
     "dg_last_error": ([], ctypes.c_char_p),
     "dg_abi_version": ([], _I32),
     "dg_kernel_launches": ([], _I64),
-    "dg_project": ([_P, _I64, _I64, _CAM, _OPT, _P, _P, _P, _P, _P, _P], _ST),
-    "dg_bin_workspace_size": ([_I64, _I64, _I32], _SZ),
-    "dg_bin_count": ([_P, _P, _I64, _P, _SZ, _I64, _I32, _P, _P], _ST),
-    "dg_bin_sort": ([_P, _P, _I64, _CAM, _I32, _P, _SZ, _I64, _P, _P, _P, _P], _ST),
-    "dg_render_fwd": ([_P, _P, _P, _CAM, _OPT, _P, _P, _P, _P, _P, _P], _ST),
-    "dg_render_bwd": ([_P, _P, _P, _CAM, _OPT, _P, _P, _P, _I64, _P, _P], _ST),
-    "dg_project_bwd": ([_P, _I64, _I64, _CAM, _OPT, _P, _P, _P, _P, _P], _ST),
+    "dg_project": ([_P, _I64, _I64, _CAM, _I32, _OPT, _P, _P, _P, _P, _P, _P], _ST),
+    "dg_bin_workspace_size": ([_I64, _I32, _I64], _SZ),
+    "dg_bin_count": ([_P, _P, _I64, _I32, _P, _SZ, _I64, _P, _P], _ST),
+    "dg_bin_sort": ([_P, _P, _I64, _CAM, _I32, _I32, _P, _SZ, _I64, _P, _P, _P, _P], _ST),
+    "dg_render_workspace_size": ([], _SZ),
+    "dg_render_fwd": ([_P, _P, _P, _CAM, _I32, _OPT, _P, _P, _P, _P, _P, _P, _SZ, _P], _ST),
+    "dg_render_bwd": ([_P, _P, _P, _CAM, _I32, _OPT, _P, _P, _P, _I64, _P, _P, _SZ, _P], _ST),
+    "dg_project_bwd": ([_P, _I64, _I64, _CAM, _I32, _OPT, _P, _P, _P, _P, _P], _ST),
     "dg_loss_workspace_size": ([_I64], _SZ),
     "dg_loss_l1": ([_P, _P, _I64, _P, _P, _P, _SZ, _P], _ST),
     "dg_loss_l1_noalloc": ([_P, _P, _I64, _P, _P, _P], _ST),
@@ -134,7 +137,7 @@ _SIGS = {
     "dg_downsample_area": ([_P, _I32, _I32, _I32, _P, _I32, _I32, _P], _ST),
     "dg_mse": ([_P, _P, _I64, _P, _P, _SZ, _P], _ST),
     "dg_opacity_reset": ([_P, _P, _P, _I64, _I64, _F, _P], _ST),
-    "dg_densify_stats": ([_P, _P, _I64, _I32, _I32, _P, _P, _P, _P], _ST),
+    "dg_densify_stats": ([_P, _P, _I64, _CAM, _I32, _P, _P, _P, _P], _ST),
     "dg_densify_workspace_size": ([_I64], _SZ),
     "dg_densify_mark": ([_P, _I64, _I64, _P, _P, _P, ctypes.POINTER(DensifyOpts), _P, _SZ, _P, _P], _ST),
     "dg_densify_apply": ([_P, _P, _P, _I64, _I64, _I64, _I64, _P, _P, _SZ, _P, _P, _P, _I64, _P, _P], _ST),
@@ -165,6 +168,22 @@ def _s(stream):
     return stream.cuda_stream
 
 
+def cameras(cams) -> ctypes.Array:
+    """A ctypes Camera array from one Camera or a sequence of them."""
+    if isinstance(cams, ctypes.Array):
+        return cams
+    if isinstance(cams, Camera):
+        cams = [cams]
+    arr = (Camera * len(cams))()
+    for k, c in enumerate(cams):
+        arr[k] = c
+    return arr
+
+
+def _c(cams):
+    return ctypes.cast(cameras(cams), _CAM)
+
+
 def _check(status):
     if status != DG_OK:
         raise DashGSError(status, _lib.dg_last_error().decode())
@@ -186,37 +205,43 @@ def dg_kernel_launches() -> int:
     return _lib.dg_kernel_launches()
 
 
-def dg_project(params, stride, P, cam, opts, feat, depth, radius, tiles, clamp, stream=None):
-    _check(_lib.dg_project(_a(params), stride, P, ctypes.byref(cam), ctypes.byref(opts), _a(feat),
-                           _a(depth), _a(radius), _a(tiles), _a(clamp), _s(stream)))
+def dg_project(params, stride, P, cams, n_views, opts, feat, depth, radius, tiles, clamp, stream=None):
+    _check(_lib.dg_project(_a(params), stride, P, _c(cams), n_views, ctypes.byref(opts), _a(feat), _a(depth),
+                           _a(radius), _a(tiles), _a(clamp), _s(stream)))
 
 
-def dg_bin_workspace_size(P, M_cap, n_tiles) -> int:
-    return _lib.dg_bin_workspace_size(P, M_cap, n_tiles)
+def dg_bin_workspace_size(P, n_views, M_cap) -> int:
+    return _lib.dg_bin_workspace_size(P, n_views, M_cap)
 
 
-def dg_bin_count(depth, tiles, P, ws, ws_bytes, M_cap, n_tiles, M_out, stream=None):
-    _check(_lib.dg_bin_count(_a(depth), _a(tiles), P, _a(ws), ws_bytes, M_cap, n_tiles, _a(M_out), _s(stream)))
+def dg_bin_count(depth, tiles, P, n_views, ws, ws_bytes, M_cap, M_out, stream=None):
+    _check(_lib.dg_bin_count(_a(depth), _a(tiles), P, n_views, _a(ws), ws_bytes, M_cap, _a(M_out), _s(stream)))
 
 
-def dg_bin_sort(feat, radius, P, cam, tile, ws, ws_bytes, M_cap, gid, ranges, status, stream=None):
-    _check(_lib.dg_bin_sort(_a(feat), _a(radius), P, ctypes.byref(cam), tile, _a(ws), ws_bytes, M_cap,
-                            _a(gid), _a(ranges), _a(status), _s(stream)))
+def dg_bin_sort(feat, radius, P, cams, n_views, tile, ws, ws_bytes, M_cap, gid, ranges, status, stream=None):
+    _check(_lib.dg_bin_sort(_a(feat), _a(radius), P, _c(cams), n_views, tile, _a(ws), ws_bytes, M_cap, _a(gid),
+                            _a(ranges), _a(status), _s(stream)))
 
 
-def dg_render_fwd(feat, gid, ranges, cam, opts, img, T_final, last, examined, blended=None, stream=None):
-    _check(_lib.dg_render_fwd(_a(feat), _a(gid), _a(ranges), ctypes.byref(cam), ctypes.byref(opts), _a(img),
-                              _a(T_final), _a(last), _a(examined), _a(blended), _s(stream)))
+def dg_render_workspace_size() -> int:
+    return _lib.dg_render_workspace_size()
 
 
-def dg_render_bwd(feat, gid, ranges, cam, opts, T_final, last, dL_dimg, P, grad2d, stream=None):
-    _check(_lib.dg_render_bwd(_a(feat), _a(gid), _a(ranges), ctypes.byref(cam), ctypes.byref(opts),
-                              _a(T_final), _a(last), _a(dL_dimg), P, _a(grad2d), _s(stream)))
+def dg_render_fwd(feat, gid, ranges, cams, n_views, opts, img, T_final, last, examined, blended, ws, ws_bytes,
+                  stream=None):
+    _check(_lib.dg_render_fwd(_a(feat), _a(gid), _a(ranges), _c(cams), n_views, ctypes.byref(opts), _a(img),
+                              _a(T_final), _a(last), _a(examined), _a(blended), _a(ws), ws_bytes, _s(stream)))
 
 
-def dg_project_bwd(params, stride, P, cam, opts, radius, clamp, grad2d, grads, stream=None):
-    _check(_lib.dg_project_bwd(_a(params), stride, P, ctypes.byref(cam), ctypes.byref(opts), _a(radius),
-                               _a(clamp), _a(grad2d), _a(grads), _s(stream)))
+def dg_render_bwd(feat, gid, ranges, cams, n_views, opts, T_final, last, dL_dimg, n_records, grad2d, ws, ws_bytes,
+                  stream=None):
+    _check(_lib.dg_render_bwd(_a(feat), _a(gid), _a(ranges), _c(cams), n_views, ctypes.byref(opts), _a(T_final),
+                              _a(last), _a(dL_dimg), n_records, _a(grad2d), _a(ws), ws_bytes, _s(stream)))
+
+
+def dg_project_bwd(params, stride, P, cams, n_views, opts, radius, clamp, grad2d, grads, stream=None):
+    _check(_lib.dg_project_bwd(_a(params), stride, P, _c(cams), n_views, ctypes.byref(opts), _a(radius), _a(clamp),
+                               _a(grad2d), _a(grads), _s(stream)))
 
 
 def dg_loss_workspace_size(n) -> int:
@@ -278,9 +303,9 @@ def dg_schedule_densify(sched: Schedule, it, P_add) -> SchedOut:
     return out
 
 
-def dg_densify_stats(grad2d, radius, P, W, H, grad_accum, denom, max_radius, stream=None):
-    _check(_lib.dg_densify_stats(_a(grad2d), _a(radius), P, W, H, _a(grad_accum), _a(denom), _a(max_radius),
-                                 _s(stream)))
+def dg_densify_stats(grad2d, radius, P, cams, n_views, grad_accum, denom, max_radius, stream=None):
+    _check(_lib.dg_densify_stats(_a(grad2d), _a(radius), P, _c(cams), n_views, _a(grad_accum), _a(denom),
+                                 _a(max_radius), _s(stream)))
 
 
 def dg_densify_workspace_size(P) -> int:

@@ -18,18 +18,32 @@ namespace dg {
 
 enum : uint8_t { F_KEEP = 1, F_CAND = 2, F_SPLIT = 4, F_SEL = 8 };
 
-__global__ void k_dstats(const float4* __restrict__ grad2d, const int* __restrict__ radius, int P, float half_w,
-                         float half_h, float* __restrict__ accum, float* __restrict__ denom, float* __restrict__ maxr)
+struct HalfSizes {
+    int n;
+    float hw[DG_MAX_VIEWS], hh[DG_MAX_VIEWS];
+};
+
+__global__ void k_dstats(const float4* __restrict__ grad2d, const int* __restrict__ radius, int P, HalfSizes hs,
+                         float* __restrict__ accum, float* __restrict__ denom, float* __restrict__ maxr)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
-    const int r = radius[i];
-    if (r <= 0) return;
-    const float4 g = grad2d[3 * (size_t)i];
-    const float gx = g.x * half_w, gy = g.y * half_h;
-    accum[i] += sqrtf(gx * gx + gy * gy);
-    denom[i] += 1.f;
-    maxr[i] = fmaxf(maxr[i], (float)r);
+    float acc = 0.f, den = 0.f, mr = maxr[i];
+    for (int v = 0; v < hs.n; ++v) {
+        const size_t r = (size_t)v * P + i;
+        const int rad = radius[r];
+        if (rad <= 0) continue;
+        const float4 g = grad2d[3 * r];
+        const float gx = g.x * hs.hw[v], gy = g.y * hs.hh[v];
+        acc += sqrtf(gx * gx + gy * gy);
+        den += 1.f;
+        mr = fmaxf(mr, (float)rad);
+    }
+    if (den > 0.f) {
+        accum[i] += acc;
+        denom[i] += den;
+        maxr[i] = mr;
+    }
 }
 
 struct DThresh {
@@ -229,14 +243,24 @@ static bool thresholds(const dg_densify_opts* o, DThresh* t)
 
 }  // namespace dg
 
-extern "C" dg_status dg_densify_stats(const float* grad2d, const int32_t* radius, int64_t P, int32_t W, int32_t H,
-                                      float* grad_accum, float* denom, float* max_radius, dg_stream stream)
+bool dg_check_cameras(const dg_camera* cams, int n_views);
+
+extern "C" dg_status dg_densify_stats(const float* grad2d, const int32_t* radius, int64_t P, const dg_camera* cams,
+                                      int32_t n_views, float* grad_accum, float* denom, float* max_radius,
+                                      dg_stream stream)
 {
-    if (P < 0 || P > INT32_MAX || W <= 0 || H <= 0) { dg_set_error("bad sizes"); return DG_ERR_ARG; }
+    if (!dg_check_cameras(cams, n_views)) return DG_ERR_ARG;
+    if (P < 0 || P > INT32_MAX) { dg_set_error("bad sizes"); return DG_ERR_ARG; }
     if (P == 0) return DG_OK;
     if (!grad2d || !radius || !grad_accum || !denom || !max_radius) { dg_set_error("null buffer"); return DG_ERR_ARG; }
+    dg::HalfSizes hs;
+    hs.n = n_views;
+    for (int v = 0; v < n_views; ++v) {
+        hs.hw[v] = 0.5f * cams[v].width;
+        hs.hh[v] = 0.5f * cams[v].height;
+    }
     dg::k_dstats<<<(int)((P + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-        (const float4*)grad2d, radius, (int)P, 0.5f * W, 0.5f * H, grad_accum, denom, max_radius);
+        (const float4*)grad2d, radius, (int)P, hs, grad_accum, denom, max_radius);
     dg_note_launch();
     return dg_check_launch("densify_stats");
 }

@@ -1,6 +1,10 @@
 // render.cu -- Eq. 1 compositing per tile (forward) and its adjoint (backward).
 //
-// One CTA per B x B tile; each thread owns PPT pixels of one column of the
+// Persistent launch over all views: one CTA per resident slot, each taking
+// (view, tile) work items from an atomic counter until none are left, so
+// tiles of very different cost (list lengths differ by orders of magnitude)
+// balance across the SMs and all views of a batch share one launch.  A work
+// item is a B x B tile; each thread owns PPT pixels of one column of the
 // tile (rows ly, ly + B/PPT, ...).  The tile's sorted list is streamed through
 // shared memory in batches of B*B/PPT records (one coalesced 48-byte gather per
 // thread per batch); every staged record is then evaluated for the thread's
@@ -63,6 +67,16 @@ __device__ inline bool tile_skip(const float4& a, const float4& b, float px0, fl
     return fmin > 2.f * logf(255.f * o) + 0.02f;
 }
 
+// 2^x on the MUFU unit (ex2.approx, flush-to-zero).
+__device__ inline float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr float kLog2e = 1.4426950408889634f;
+
 // Stable block-wide compaction index of `keep`; *total = number kept.  Ends with a barrier.
 template <int NT>
 __device__ inline int compact_index(bool keep, int* s_w, int* total)
@@ -84,10 +98,44 @@ __device__ inline int compact_index(bool keep, int* s_w, int* total)
     return pre + __popc(bal & ((1u << lane) - 1u));
 }
 
+// Views of one launch: image sizes, tile grids and where each view's tiles and
+// pixels start in the global tile range table and the concatenated images.
+struct RViews {
+    int n;
+    int total;                      // work items = tiles of all views
+    int W[DG_MAX_VIEWS], H[DG_MAX_VIEWS], TX[DG_MAX_VIEWS];
+    int toff[DG_MAX_VIEWS + 1];
+    long long poff[DG_MAX_VIEWS];   // first pixel of each view
+    float bg0, bg1, bg2;
+};
+
+struct Item { int tile, v, tx, ty, W, H; long long poff; };
+
+// Next work item of this CTA (item.tile < 0: none left).  Ends with a barrier.
+__device__ inline Item next_item(int* counter, const RViews& rv, int* s_item)
+{
+    if (threadIdx.x == 0) *s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    Item it;
+    it.tile = *s_item;
+    __syncthreads();
+    if (it.tile >= rv.total) { it.tile = -1; return it; }
+    int v = 0;
+    while (v + 1 < rv.n && it.tile >= rv.toff[v + 1]) ++v;
+    const int t = it.tile - rv.toff[v];
+    it.v = v;
+    it.tx = t % rv.TX[v];
+    it.ty = t / rv.TX[v];
+    it.W = rv.W[v];
+    it.H = rv.H[v];
+    it.poff = rv.poff[v];
+    return it;
+}
+
 template <int B, int PPT>
 __global__ void __launch_bounds__(B * B / PPT)
 k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
-             const uint2* __restrict__ ranges, int W, int H, int TX, float bg0, float bg1, float bg2,
+             const uint2* __restrict__ ranges, RViews rv, int* __restrict__ counter,
              float* __restrict__ img, float* __restrict__ Tout, int* __restrict__ lastout,
              int* __restrict__ exout, int* __restrict__ blout)
 {
@@ -98,8 +146,11 @@ k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
     __shared__ float s_c[NT];   // b
     __shared__ int s_pos[NT];   // list position
     __shared__ int s_w[NT / 32];
-    const int tile = blockIdx.x;
-    const int tx = tile % TX, ty = tile / TX;
+    __shared__ int s_item;
+    for (;;) {
+    const Item it = next_item(counter, rv, &s_item);
+    if (it.tile < 0) break;
+    const int tile = it.tile, tx = it.tx, ty = it.ty, W = it.W, H = it.H;
     const int x = tx * B + (int)(threadIdx.x % B);
     const int y0 = ty * B + (int)(threadIdx.x / B);
     const float pxc = (float)x + 0.5f;
@@ -137,8 +188,9 @@ k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
         int cnt;
         const int slot = compact_index<NT>(keep, s_w, &cnt);
         if (keep) {
-            s_a[slot] = ga;
-            s_b[slot] = gb;
+            // prescaled: p = log2(e) * power = dx (a' dx + b' dy) + c' dy^2, alpha = 2^(p + log2 o)
+            s_a[slot] = make_float4(ga.x, ga.y, -0.5f * kLog2e * ga.z, -kLog2e * ga.w);
+            s_b[slot] = make_float4(-0.5f * kLog2e * gb.x, __log2f(gb.y), gb.z, gb.w);
             s_c[slot] = gc;
             s_pos[slot] = j;
         }
@@ -149,15 +201,16 @@ k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
             const float cb = s_c[kk];
             const int pos = s_pos[kk];
             const float dx = a.x - pxc;
+            const float adx = a.z * dx;
             alldone = true;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 if (!done[k]) {
                     const float dy = a.y - pyc[k];
-                    const float power = -0.5f * (a.z * dx * dx + b.x * dy * dy) - a.w * dx * dy;
-                    const float alpha = fminf(kAlphaMax, b.y * __expf(power));
-                    if (power <= 0.f && alpha >= kAlphaMin) {
-                        const float Tn = T[k] * (1.f - alpha);
+                    const float p = fmaf(dx, fmaf(a.w, dy, adx), b.x * dy * dy);
+                    const float alpha = fminf(kAlphaMax, ex2_approx(p + b.y));
+                    if (p <= 0.f && alpha >= kAlphaMin) {
+                        const float Tn = fmaf(-alpha, T[k], T[k]);
                         if (Tn < kTMin) {
                             done[k] = true;
                             stop[k] = pos;
@@ -177,21 +230,23 @@ k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
         }
     }
     const size_t HW = (size_t)W * H;
+    float* im = img + 3 * it.poff;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         const int y = y0 + k * RSTEP;
         if (x < W && y < H) {
             const size_t pix = (size_t)y * W + x;
-            img[pix] = c0[k] + T[k] * bg0;
-            img[HW + pix] = c1[k] + T[k] * bg1;
-            img[2 * HW + pix] = c2[k] + T[k] * bg2;
-            Tout[pix] = T[k];
-            lastout[pix] = last[k];
+            im[pix] = c0[k] + T[k] * rv.bg0;
+            im[HW + pix] = c1[k] + T[k] * rv.bg1;
+            im[2 * HW + pix] = c2[k] + T[k] * rv.bg2;
+            Tout[it.poff + pix] = T[k];
+            lastout[it.poff + pix] = last[k];
             // entries visited: up to and including the one that stopped compositing
-            if (exout) exout[pix] = stop[k] >= 0 ? stop[k] + 1 : n;
-            if (blout) blout[pix] = nbl[k];
+            if (exout) exout[it.poff + pix] = stop[k] >= 0 ? stop[k] + 1 : n;
+            if (blout) blout[it.poff + pix] = nbl[k];
         }
     }
+    }  // work items
 }
 
 // Sum of 9 per-lane values over the warp by recursive halving: at each step a
@@ -239,7 +294,7 @@ __device__ inline float warp_sum9(const float v[9], int lane, int* idx)
 template <int B, int PPT>
 __global__ void __launch_bounds__(B * B / PPT)
 k_render_bwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
-             const uint2* __restrict__ ranges, int W, int H, int TX, float bg0, float bg1, float bg2,
+             const uint2* __restrict__ ranges, RViews rv, int* __restrict__ counter,
              const float* __restrict__ Tfin, const int* __restrict__ lastin,
              const float* __restrict__ dLdimg, float4* __restrict__ grad2d)
 {
@@ -252,8 +307,12 @@ k_render_bwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
     __shared__ int s_pos[NT];
     __shared__ int s_w[NT / 32];
     __shared__ int s_n;
-    const int tile = blockIdx.x;
-    const int tx = tile % TX, ty = tile / TX;
+    __shared__ int s_item;
+    const float bg0 = rv.bg0, bg1 = rv.bg1, bg2 = rv.bg2;
+    for (;;) {
+    const Item it = next_item(counter, rv, &s_item);
+    if (it.tile < 0) break;
+    const int tile = it.tile, tx = it.tx, ty = it.ty, W = it.W, H = it.H;
     const int x = tx * B + (int)(threadIdx.x % B);
     const int y0 = ty * B + (int)(threadIdx.x / B);
     const float pxc = (float)x + 0.5f;
@@ -271,11 +330,12 @@ k_render_bwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
         T[k] = 1.f; g0[k] = g1[k] = g2[k] = 0.f; lastp[k] = 0;
         if (x < W && y < H) {
             const size_t pix = (size_t)y * W + x;
-            T[k] = Tfin[pix];
-            lastp[k] = lastin[pix];
-            g0[k] = dLdimg[pix];
-            g1[k] = dLdimg[HW + pix];
-            g2[k] = dLdimg[2 * HW + pix];
+            const float* dl = dLdimg + 3 * it.poff;
+            T[k] = Tfin[it.poff + pix];
+            lastp[k] = lastin[it.poff + pix];
+            g0[k] = dl[pix];
+            g1[k] = dl[HW + pix];
+            g2[k] = dl[2 * HW + pix];
         }
         S0[k] = T[k] * bg0; S1[k] = T[k] * bg1; S2[k] = T[k] * bg2;  // colour behind the current entry
         mylast = max(mylast, lastp[k]);
@@ -360,30 +420,63 @@ k_render_bwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
         }
         __syncthreads();
     }
+    }  // work items
 }
 
 }  // namespace dg
 
-template <int B, int PPT>
-static void launch_fwd(const float* feat, const uint32_t* gid, const uint32_t* ranges, const dg_camera* cam,
-                       const dg_raster_opts* o, float* img, float* T, int* last, int* ex, int* bl, cudaStream_t s)
+static dg::RViews make_rviews(const dg_camera* cams, int n, int B, const dg_raster_opts* o)
 {
-    const int TX = (cam->width + B - 1) / B, TY = (cam->height + B - 1) / B;
-    dg::k_render_fwd<B, PPT><<<TX * TY, B * B / PPT, 0, s>>>((const float4*)feat, gid, (const uint2*)ranges,
-                                                             cam->width, cam->height, TX, o->bg[0], o->bg[1],
-                                                             o->bg[2], img, T, last, ex, bl);
+    dg::RViews rv;
+    rv.n = n;
+    int tiles = 0;
+    long long pix = 0;
+    for (int v = 0; v < n; ++v) {
+        rv.W[v] = cams[v].width;
+        rv.H[v] = cams[v].height;
+        rv.TX[v] = (cams[v].width + B - 1) / B;
+        rv.toff[v] = tiles;
+        rv.poff[v] = pix;
+        tiles += rv.TX[v] * ((cams[v].height + B - 1) / B);
+        pix += (long long)cams[v].width * cams[v].height;
+    }
+    rv.toff[n] = tiles;
+    rv.total = tiles;
+    rv.bg0 = o->bg[0]; rv.bg1 = o->bg[1]; rv.bg2 = o->bg[2];
+    return rv;
+}
+
+// CTAs of a persistent launch: every resident slot of the device, at most one per item.
+template <typename Kern>
+static int persistent_grid(Kern kern, int threads, int items)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+    long long g = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    if (g > items) g = items;
+    return (int)(g > 0 ? g : 1);
+}
+
+template <int B, int PPT>
+static void launch_fwd(const float* feat, const uint32_t* gid, const uint32_t* ranges, const dg::RViews& rv,
+                       int* counter, float* img, float* T, int* last, int* ex, int* bl, cudaStream_t s)
+{
+    auto kern = dg::k_render_fwd<B, PPT>;
+    const int grid = persistent_grid(kern, B * B / PPT, rv.total);
+    kern<<<grid, B * B / PPT, 0, s>>>((const float4*)feat, gid, (const uint2*)ranges, rv, counter, img, T, last, ex, bl);
     dg_note_launch();
 }
 
 template <int B, int PPT>
-static void launch_bwd(const float* feat, const uint32_t* gid, const uint32_t* ranges, const dg_camera* cam,
-                       const dg_raster_opts* o, const float* T, const int* last, const float* dL, float* g2,
-                       cudaStream_t s)
+static void launch_bwd(const float* feat, const uint32_t* gid, const uint32_t* ranges, const dg::RViews& rv,
+                       int* counter, const float* T, const int* last, const float* dL, float* g2, cudaStream_t s)
 {
-    const int TX = (cam->width + B - 1) / B, TY = (cam->height + B - 1) / B;
-    dg::k_render_bwd<B, PPT><<<TX * TY, B * B / PPT, 0, s>>>((const float4*)feat, gid, (const uint2*)ranges,
-                                                             cam->width, cam->height, TX, o->bg[0], o->bg[1],
-                                                             o->bg[2], T, last, dL, (float4*)g2);
+    auto kern = dg::k_render_bwd<B, PPT>;
+    const int grid = persistent_grid(kern, B * B / PPT, rv.total);
+    kern<<<grid, B * B / PPT, 0, s>>>((const float4*)feat, gid, (const uint2*)ranges, rv, counter, T, last, dL,
+                                      (float4*)g2);
     dg_note_launch();
 }
 
@@ -397,48 +490,59 @@ static int resolve_ppt(const dg_raster_opts* o, bool backward)
     return backward ? 4 : 2;
 }
 
-static bool render_args(const dg_camera* cam, const dg_raster_opts* opts)
+bool dg_check_cameras(const dg_camera* cams, int n_views);
+
+static bool render_args(const dg_camera* cams, int n_views, const dg_raster_opts* opts, void* ws, size_t ws_bytes)
 {
-    if (!cam || !opts) { dg_set_error("camera/opts null"); return false; }
-    if (cam->width <= 0 || cam->height <= 0) { dg_set_error("bad image size"); return false; }
+    if (!dg_check_cameras(cams, n_views)) return false;
+    if (!opts) { dg_set_error("opts null"); return false; }
     if (opts->tile != 8 && opts->tile != 16) { dg_set_error("render supports tile 8 or 16, got %d", opts->tile); return false; }
     const int p = opts->pixels_per_thread;
     if (p != 0 && p != 1 && p != 2 && p != 4) { dg_set_error("pixels_per_thread must be 0, 1, 2 or 4, got %d", p); return false; }
+    if (!ws || ws_bytes < dg_render_workspace_size()) { dg_set_error("render workspace missing or too small"); return false; }
     return true;
 }
 
+extern "C" size_t dg_render_workspace_size(void) { return 256; }
+
 extern "C" dg_status dg_render_fwd(const float* feat, const uint32_t* gid, const uint32_t* ranges,
-                                   const dg_camera* cam, const dg_raster_opts* opts, float* img,
-                                   float* T_final, int32_t* last, int32_t* examined, int32_t* blended,
-                                   dg_stream stream)
+                                   const dg_camera* cams, int32_t n_views, const dg_raster_opts* opts, float* img,
+                                   float* T_final, int32_t* last, int32_t* examined, int32_t* blended, void* ws,
+                                   size_t ws_bytes, dg_stream stream)
 {
-    if (!render_args(cam, opts)) return DG_ERR_ARG;
+    if (!render_args(cams, n_views, opts, ws, ws_bytes)) return DG_ERR_ARG;
     if (!ranges || !img || !T_final || !last) { dg_set_error("null buffer"); return DG_ERR_ARG; }
     if (feat && (((uintptr_t)feat) & 15u)) { dg_set_error("feat must be 16-byte aligned"); return DG_ERR_ARG; }
     cudaStream_t s = (cudaStream_t)stream;
+    const dg::RViews rv = make_rviews(cams, n_views, opts->tile, opts);
+    int* counter = (int*)ws;
+    cudaMemsetAsync(counter, 0, sizeof(int), s);
     const int ppt = resolve_ppt(opts, false);
-    if (opts->tile == 8) launch_fwd<8, 1>(feat, gid, ranges, cam, opts, img, T_final, last, examined, blended, s);
-    else if (ppt == 1) launch_fwd<16, 1>(feat, gid, ranges, cam, opts, img, T_final, last, examined, blended, s);
-    else if (ppt == 2) launch_fwd<16, 2>(feat, gid, ranges, cam, opts, img, T_final, last, examined, blended, s);
-    else launch_fwd<16, 4>(feat, gid, ranges, cam, opts, img, T_final, last, examined, blended, s);
+    if (opts->tile == 8) launch_fwd<8, 1>(feat, gid, ranges, rv, counter, img, T_final, last, examined, blended, s);
+    else if (ppt == 1) launch_fwd<16, 1>(feat, gid, ranges, rv, counter, img, T_final, last, examined, blended, s);
+    else if (ppt == 2) launch_fwd<16, 2>(feat, gid, ranges, rv, counter, img, T_final, last, examined, blended, s);
+    else launch_fwd<16, 4>(feat, gid, ranges, rv, counter, img, T_final, last, examined, blended, s);
     return dg_check_launch("render_fwd");
 }
 
 extern "C" dg_status dg_render_bwd(const float* feat, const uint32_t* gid, const uint32_t* ranges,
-                                   const dg_camera* cam, const dg_raster_opts* opts, const float* T_final,
-                                   const int32_t* last, const float* dL_dimg, int64_t P, float* grad2d,
-                                   dg_stream stream)
+                                   const dg_camera* cams, int32_t n_views, const dg_raster_opts* opts,
+                                   const float* T_final, const int32_t* last, const float* dL_dimg, int64_t n_records,
+                                   float* grad2d, void* ws, size_t ws_bytes, dg_stream stream)
 {
-    if (!render_args(cam, opts)) return DG_ERR_ARG;
-    if (P < 0) { dg_set_error("P < 0"); return DG_ERR_ARG; }
-    if (!ranges || !T_final || !last || !dL_dimg || (P > 0 && !grad2d)) { dg_set_error("null buffer"); return DG_ERR_ARG; }
+    if (!render_args(cams, n_views, opts, ws, ws_bytes)) return DG_ERR_ARG;
+    if (n_records < 0) { dg_set_error("n_records < 0"); return DG_ERR_ARG; }
+    if (!ranges || !T_final || !last || !dL_dimg || (n_records > 0 && !grad2d)) { dg_set_error("null buffer"); return DG_ERR_ARG; }
     if (grad2d && (((uintptr_t)grad2d) & 15u)) { dg_set_error("grad2d must be 16-byte aligned"); return DG_ERR_ARG; }
     cudaStream_t s = (cudaStream_t)stream;
-    if (P > 0) cudaMemsetAsync(grad2d, 0, sizeof(float) * DG_FEAT_FLOATS * (size_t)P, s);
+    if (n_records > 0) cudaMemsetAsync(grad2d, 0, sizeof(float) * DG_FEAT_FLOATS * (size_t)n_records, s);
+    const dg::RViews rv = make_rviews(cams, n_views, opts->tile, opts);
+    int* counter = (int*)ws;
+    cudaMemsetAsync(counter, 0, sizeof(int), s);
     const int ppt = resolve_ppt(opts, true);
-    if (opts->tile == 8) launch_bwd<8, 1>(feat, gid, ranges, cam, opts, T_final, last, dL_dimg, grad2d, s);
-    else if (ppt == 1) launch_bwd<16, 1>(feat, gid, ranges, cam, opts, T_final, last, dL_dimg, grad2d, s);
-    else if (ppt == 2) launch_bwd<16, 2>(feat, gid, ranges, cam, opts, T_final, last, dL_dimg, grad2d, s);
-    else launch_bwd<16, 4>(feat, gid, ranges, cam, opts, T_final, last, dL_dimg, grad2d, s);
+    if (opts->tile == 8) launch_bwd<8, 1>(feat, gid, ranges, rv, counter, T_final, last, dL_dimg, grad2d, s);
+    else if (ppt == 1) launch_bwd<16, 1>(feat, gid, ranges, rv, counter, T_final, last, dL_dimg, grad2d, s);
+    else if (ppt == 2) launch_bwd<16, 2>(feat, gid, ranges, rv, counter, T_final, last, dL_dimg, grad2d, s);
+    else launch_bwd<16, 4>(feat, gid, ranges, rv, counter, T_final, last, dL_dimg, grad2d, s);
     return dg_check_launch("render_bwd");
 }

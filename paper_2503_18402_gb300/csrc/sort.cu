@@ -9,6 +9,11 @@
 //      (ceil(log2(tiles)) bits: 2 passes at 1237x822 / 16^2 = 4056 tiles).
 // Stability of stage 2 preserves the depth order inside each tile, so the
 // result equals the lexicographic (tile, depth bits, index) order.
+// Several views: records are r = v * P + i; stage 1 adds one stable pass on
+// the view index after the depth passes (order (view, depth, index)) and the
+// tile ids are global, view_offset[v] + ty * TX_v + tx, so each view's tiles
+// form one contiguous block of the range table.  The pair payload is the
+// record index r.
 //
 // Radix pass = per-block digit histogram, exclusive scan of the
 // digit-major histogram, stable scatter.  Each warp owns a contiguous
@@ -20,26 +25,39 @@
 namespace dg {
 
 // --------------------------------------------------------------- binning
-__global__ void k_depth_keys(const float* __restrict__ depth, const int* __restrict__ tiles, int P,
+__global__ void k_depth_keys(const float* __restrict__ depth, const int* __restrict__ tiles, long long N,
                              uint32_t* __restrict__ keys, uint32_t* __restrict__ idx)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P) return;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
     keys[i] = tiles[i] > 0 ? __float_as_uint(depth[i]) : 0xffffffffu;
     idx[i] = (uint32_t)i;
 }
 
+// view index of each depth-ordered record, for the stable view pass
+__global__ void k_view_keys(const uint32_t* __restrict__ rec, long long N, uint32_t P, uint32_t* __restrict__ keys)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) keys[i] = rec[i] / P;
+}
+
+struct TileGrid {
+    int n;
+    int TX[DG_MAX_VIEWS], TY[DG_MAX_VIEWS];
+    int off[DG_MAX_VIEWS + 1];  // first global tile id of each view
+};
+
 // First sorted position whose pair range holds each RS_TILE block's first pair.
-__global__ void k_block_starts(const uint64_t* __restrict__ poff, int P, const long long* M_dev, long long M_cap,
+__global__ void k_block_starts(const uint64_t* __restrict__ poff, long long P, const long long* M_dev, long long M_cap,
                                int* __restrict__ bstart)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long M = *M_dev;
     if (s >= P || M > M_cap) return;
     const long long a = (long long)poff[s];
     const long long e = s + 1 < P ? (long long)poff[s + 1] : M;
     if (e <= a) return;
-    for (long long b = (a + RS_TILE - 1) / RS_TILE; b * RS_TILE < e; ++b) bstart[b] = s;
+    for (long long b = (a + RS_TILE - 1) / RS_TILE; b * RS_TILE < e; ++b) bstart[b] = (int)s;
 }
 
 // Pair emission, one RS_TILE block of consecutive pairs per CTA.  The block's
@@ -49,14 +67,16 @@ __global__ void k_block_starts(const uint64_t* __restrict__ poff, int P, const l
 // and the per-block histogram of the first radix digit.
 __global__ void __launch_bounds__(RS_THREADS)
 k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const uint32_t* __restrict__ order,
-       const uint64_t* __restrict__ poff, const int* __restrict__ bstart, int P, const long long* M_dev,
-       long long M_cap, int B, int TX, int TY, uint32_t mask0, uint32_t* __restrict__ pkey,
+       const uint64_t* __restrict__ poff, const int* __restrict__ bstart, long long P, uint32_t Pv,
+       const long long* M_dev, long long M_cap, int B, TileGrid tg, uint32_t mask0, uint32_t* __restrict__ pkey,
        uint32_t* __restrict__ pval, uint32_t* __restrict__ hist0, int nblk, int* status)
 {
     __shared__ int w_start[RS_TILE];      // pair offset of each staged Gaussian, relative to the block
     __shared__ uint32_t w_xy[RS_TILE];    // rect x0 | y0 << 16
     __shared__ int w_wx[RS_TILE];         // rect width in tiles
-    __shared__ uint32_t w_g[RS_TILE];     // Gaussian index
+    __shared__ uint32_t w_g[RS_TILE];     // record index
+    __shared__ int w_base[RS_TILE];       // global tile id of the view's tile (0, 0)
+    __shared__ int w_tx[RS_TILE];         // tiles per row of the view
     __shared__ uint32_t h[1 << RS_MAXBITS];
     const long long M = *M_dev;
     if (M > M_cap) {
@@ -75,17 +95,20 @@ k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const ui
         // stage the Gaussians whose pair range starts before `end` (a prefix of s_lo, s_lo+1, ...)
         int top = 0;
         for (int w = threadIdx.x; w < RS_TILE; w += RS_THREADS) {
-            const int s = s_lo + w;
+            const long long s = (long long)s_lo + w;
             if (s >= P) break;
             const long long st = (long long)poff[s];
             if (st >= end) break;
             const uint32_t g = order[s];
+            const int v = (int)(g / Pv);
             const float4 f0 = feat[3 * (size_t)g];
-            const Rect q = tile_rect(f0.x, f0.y, radius[g], B, TX, TY);
+            const Rect q = tile_rect(f0.x, f0.y, radius[g], B, tg.TX[v], tg.TY[v]);
             w_start[w] = (int)(st - base);
             w_xy[w] = (uint32_t)q.x0 | ((uint32_t)q.y0 << 16);
             w_wx[w] = q.x1 - q.x0;
             w_g[w] = g;
+            w_base[w] = tg.off[v];
+            w_tx[w] = tg.TX[v];
             top = w + 1;
         }
         if (top > 0) atomicMax(&s_nw, top);
@@ -105,6 +128,7 @@ k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const ui
             int wx = w_wx[lo];
             uint32_t xy = w_xy[lo];
             uint32_t g = w_g[lo];
+            int tb = w_base[lo], TXv = w_tx[lo];
             int next = lo + 1 < nw ? w_start[lo + 1] : nblock;
             int ry = j / wx, rx = j - ry * wx;
             uint32_t kk[RS_IPT], vv[RS_IPT];
@@ -115,10 +139,11 @@ k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const ui
                     if (rel0 + e >= next) {  // next Gaussian of the window
                         ++lo;
                         wx = w_wx[lo]; xy = w_xy[lo]; g = w_g[lo];
+                        tb = w_base[lo]; TXv = w_tx[lo];
                         next = lo + 1 < nw ? w_start[lo + 1] : nblock;
                         rx = 0; ry = 0;
                     }
-                    const uint32_t key = (uint32_t)(((int)(xy >> 16) + ry) * TX + (int)(xy & 0xffffu) + rx);
+                    const uint32_t key = (uint32_t)(tb + ((int)(xy >> 16) + ry) * TXv + (int)(xy & 0xffffu) + rx);
                     kk[e] = key;
                     vv[e] = g;
                     atomicAdd(&h[key & mask0], 1u);
@@ -215,56 +240,93 @@ static BinWs bin_layout(char* base, long long P, long long M_cap)
     return w;
 }
 
-}  // namespace dg
+// Where phase 1 leaves the (view, depth, index) order of the records.
+static uint32_t* order_buffer(const BinWs& w, int n_views) { return n_views > 1 ? w.dv1 : w.dv0; }
 
-extern "C" size_t dg_bin_workspace_size(int64_t P, int64_t M_cap, int32_t n_tiles)
+static int view_bits(int n_views)
 {
-    (void)n_tiles;
-    if (P < 0 || M_cap < 0) return 0;
-    return dg::bin_layout(nullptr, P, M_cap).bytes;
+    int b = 0;
+    while ((1 << b) < n_views) ++b;
+    return b;
 }
 
-extern "C" dg_status dg_bin_count(const float* depth, const int32_t* tiles, int64_t P, void* ws,
-                                  size_t ws_bytes, int64_t M_cap, int32_t n_tiles, int64_t* M_out,
-                                  dg_stream stream)
+}  // namespace dg
+
+extern "C" size_t dg_bin_workspace_size(int64_t P, int32_t n_views, int64_t M_cap)
 {
-    if (P < 0 || P > INT32_MAX || M_cap < 0 || M_cap > (int64_t)UINT32_MAX || n_tiles < 1) {
-        dg_set_error("bad sizes P=%lld M_cap=%lld n_tiles=%d", (long long)P, (long long)M_cap, n_tiles);
+    if (P < 0 || M_cap < 0 || n_views < 1 || n_views > DG_MAX_VIEWS) return 0;
+    return dg::bin_layout(nullptr, P * n_views, M_cap).bytes;
+}
+
+extern "C" dg_status dg_bin_count(const float* depth, const int32_t* tiles, int64_t P, int32_t n_views, void* ws,
+                                  size_t ws_bytes, int64_t M_cap, int64_t* M_out, dg_stream stream)
+{
+    if (P < 0 || n_views < 1 || n_views > DG_MAX_VIEWS || P * n_views > (int64_t)UINT32_MAX || M_cap < 0 ||
+        M_cap > (int64_t)UINT32_MAX) {
+        dg_set_error("bad sizes P=%lld n_views=%d M_cap=%lld", (long long)P, n_views, (long long)M_cap);
         return DG_ERR_ARG;
     }
     if (!ws || !M_out || (P > 0 && (!depth || !tiles))) { dg_set_error("null buffer"); return DG_ERR_ARG; }
-    const dg::BinWs w = dg::bin_layout((char*)ws, P, M_cap);
+    const long long N = P * n_views;
+    const dg::BinWs w = dg::bin_layout((char*)ws, N, M_cap);
     if (ws_bytes < w.bytes) { dg_set_error("workspace %zu < %zu bytes", ws_bytes, w.bytes); return DG_ERR_CAPACITY; }
     cudaStream_t s = (cudaStream_t)stream;
-    if (P == 0) {
+    if (N == 0) {
         cudaMemsetAsync(w.M, 0, sizeof(long long), s);
         cudaMemsetAsync(M_out, 0, sizeof(long long), s);
         return dg_check_launch("bin_count");
     }
-    dg::k_depth_keys<<<(int)((P + 255) / 256), 256, 0, s>>>(depth, tiles, (int)P, w.dk0, w.dv0);
+    const int nb = (int)((N + 255) / 256);
+    dg::k_depth_keys<<<nb, 256, 0, s>>>(depth, tiles, N, w.dk0, w.dv0);
     dg_note_launch();
     dg::SortBufs sb{w.hist, w.bsum};
     // 32 key bits = 4 passes ping-ponging dk0 -> dk1 -> dk0 -> dk1 -> dk0: the
-    // depth order ends in dv0 (checked below so a change of pass count cannot
-    // silently move it).
-    const dg::KV r = dg::radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, nullptr, nullptr, nullptr, P, 32, sb, s);
+    // depth order ends in dv0 (checked so a change of pass count cannot move it)
+    const dg::KV r = dg::radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, nullptr, nullptr, nullptr, N, 32, sb, s);
     if (r.v != w.dv0) { dg_set_error("internal: depth order buffer"); return DG_ERR_CUDA; }
-    dg::exclusive_scan(dg::LoadTilesInOrder{tiles, w.dv0}, P, w.poff, w.bsum, w.M, s);
+    if (n_views > 1) {
+        // stable pass on the view index: (view, depth, index), result in dv1
+        dg::k_view_keys<<<nb, 256, 0, s>>>(w.dv0, N, (uint32_t)P, w.dk1);
+        dg_note_launch();
+        const dg::KV r2 = dg::radix_sort(w.dk1, w.dv0, w.dk0, w.dv1, nullptr, nullptr, nullptr, N,
+                                         dg::view_bits(n_views), sb, s);
+        if (r2.v != w.dv1) { dg_set_error("internal: view order buffer"); return DG_ERR_CUDA; }
+    }
+    dg::exclusive_scan(dg::LoadTilesInOrder{tiles, dg::order_buffer(w, n_views)}, N, w.poff, w.bsum, w.M, s);
     cudaMemcpyAsync(M_out, w.M, sizeof(long long), cudaMemcpyDeviceToDevice, s);
     return dg_check_launch("bin_count");
 }
 
-extern "C" dg_status dg_bin_sort(const float* feat, const int32_t* radius, int64_t P, const dg_camera* cam,
-                                 int32_t tile, void* ws, size_t ws_bytes, int64_t M_cap, uint32_t* gid,
-                                 uint32_t* ranges, int32_t* status, dg_stream stream)
+bool dg_check_cameras(const dg_camera* cams, int n_views);
+
+extern "C" dg_status dg_bin_sort(const float* feat, const int32_t* radius, int64_t P, const dg_camera* cams,
+                                 int32_t n_views, int32_t tile, void* ws, size_t ws_bytes, int64_t M_cap,
+                                 uint32_t* gid, uint32_t* ranges, int32_t* status, dg_stream stream)
 {
-    if (!cam || tile < 1 || cam->width <= 0 || cam->height <= 0) { dg_set_error("bad camera or tile"); return DG_ERR_ARG; }
-    if (P < 0 || P > INT32_MAX || M_cap < 0 || M_cap > (int64_t)UINT32_MAX) { dg_set_error("bad sizes"); return DG_ERR_ARG; }
-    if (!ws || !ranges || !status || (P > 0 && (!feat || !radius)) || (M_cap > 0 && !gid)) { dg_set_error("null buffer"); return DG_ERR_ARG; }
-    const dg::BinWs w = dg::bin_layout((char*)ws, P, M_cap);
+    if (!dg_check_cameras(cams, n_views)) return DG_ERR_ARG;
+    if (tile < 1 || tile > 64) { dg_set_error("bad tile %d", tile); return DG_ERR_ARG; }
+    if (P < 0 || P * n_views > (int64_t)UINT32_MAX || M_cap < 0 || M_cap > (int64_t)UINT32_MAX) {
+        dg_set_error("bad sizes");
+        return DG_ERR_ARG;
+    }
+    if (!ws || !ranges || !status || (P > 0 && (!feat || !radius)) || (M_cap > 0 && !gid)) {
+        dg_set_error("null buffer");
+        return DG_ERR_ARG;
+    }
+    const long long N = P * n_views;
+    const dg::BinWs w = dg::bin_layout((char*)ws, N, M_cap);
     if (ws_bytes < w.bytes) { dg_set_error("workspace %zu < %zu bytes", ws_bytes, w.bytes); return DG_ERR_CAPACITY; }
-    const int TX = (cam->width + tile - 1) / tile, TY = (cam->height + tile - 1) / tile;
-    const long long n_tiles = (long long)TX * TY;
+    dg::TileGrid tg;
+    tg.n = n_views;
+    long long n_tiles = 0;
+    for (int v = 0; v < n_views; ++v) {
+        tg.TX[v] = (cams[v].width + tile - 1) / tile;
+        tg.TY[v] = (cams[v].height + tile - 1) / tile;
+        tg.off[v] = (int)n_tiles;
+        n_tiles += (long long)tg.TX[v] * tg.TY[v];
+    }
+    tg.off[n_views] = (int)n_tiles;
+    if (n_tiles > (1ll << 30)) { dg_set_error("too many tiles"); return DG_ERR_ARG; }
     cudaStream_t s = (cudaStream_t)stream;
     cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * n_tiles, s);
     cudaMemsetAsync(status, 0, sizeof(int32_t), s);
@@ -273,15 +335,16 @@ extern "C" dg_status dg_bin_sort(const float* feat, const int32_t* radius, int64
     const int b0 = dg::first_pass_bits(bits);
     const uint32_t mask0 = b0 > 0 ? (1u << b0) - 1u : 0u;
     const int nblk = (int)((M_cap + dg::RS_TILE - 1) / dg::RS_TILE);
-    const int pb = (int)((P + 255) / 256);
-    if (P > 0 && nblk > 0) {
-        dg::k_block_starts<<<pb, 256, 0, s>>>(w.poff, (int)P, w.M, M_cap, w.bstart);
+    const int pb = (int)((N + 255) / 256);
+    uint32_t* order = dg::order_buffer(w, n_views);
+    if (N > 0 && nblk > 0) {
+        dg::k_block_starts<<<pb, 256, 0, s>>>(w.poff, N, w.M, M_cap, w.bstart);
         dg_note_launch();
     }
-    // emit pairs in depth order (slots from phase 1) with pass-0 histogram, or flag overflow
-    dg::k_emit<<<nblk > 0 ? nblk : 1, dg::RS_THREADS, 0, s>>>((const float4*)feat, radius, w.dv0, w.poff, w.bstart,
-                                                            (int)P, w.M, M_cap, tile, TX, TY, mask0, w.pk0, w.pv0,
-                                                            w.hist, nblk > 0 ? nblk : 1, status);
+    // emit pairs in (view, depth) order (slots from phase 1) with pass-0 histogram, or flag overflow
+    dg::k_emit<<<nblk > 0 ? nblk : 1, dg::RS_THREADS, 0, s>>>((const float4*)feat, radius, order, w.poff, w.bstart,
+                                                            N, (uint32_t)(P > 0 ? P : 1), w.M, M_cap, tile, tg, mask0,
+                                                            w.pk0, w.pv0, w.hist, nblk > 0 ? nblk : 1, status);
     dg_note_launch();
     if (M_cap == 0) return dg_check_launch("bin_sort");
     dg::SortBufs sb{w.hist, w.bsum};

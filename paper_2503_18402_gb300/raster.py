@@ -1,14 +1,15 @@
 """Python glue around the C ABI: buffer management and torch.autograd.
 
-``Rasterizer`` owns the device buffers of one view (projected records,
-binning workspace, pair list, per-pixel state) and grows them on demand;
-every step of the computation runs in the CUDA library through ``capi``.
-``rasterize`` is the differentiable entry point: a ``torch.autograd.Function``
-whose backward calls dg_render_bwd and dg_project_bwd.
+``Rasterizer`` owns the device buffers of one batch of views (projected
+records, binning workspace, pair list, per-pixel state) and grows them on
+demand; every step of the computation runs in the CUDA library through
+``capi``.  ``rasterize`` is the differentiable entry point: a
+``torch.autograd.Function`` whose backward calls dg_render_bwd and
+dg_project_bwd.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass
+from dataclasses import dataclass, field
 
 import torch
 
@@ -24,17 +25,26 @@ def make_camera(viewmat, intr, width, height) -> capi.Camera:
 
 @dataclass
 class Frame:
-    """Per-view forward state kept for the backward pass."""
+    """Forward state of one batch of views, kept for the backward pass.
+    With one view, img/T/last are shaped (3, H, W)/(H, W)/(H, W); with several
+    they are the flat concatenations and `images`, `Ts`, `lasts` hold the
+    per-view slices."""
     P: int
-    cam: capi.Camera
-    img: torch.Tensor       # (3, H, W)
-    T: torch.Tensor         # (H, W)
-    last: torch.Tensor      # (H, W) int32
-    M: int                  # number of (tile, Gaussian) pairs
+    cams: list
+    img: torch.Tensor
+    T: torch.Tensor
+    last: torch.Tensor
+    M: int
+    flat_img: torch.Tensor = None
+    flat_T: torch.Tensor = None
+    flat_last: torch.Tensor = None
+    images: list = field(default_factory=list)
+    Ts: list = field(default_factory=list)
+    lasts: list = field(default_factory=list)
 
 
 class Rasterizer:
-    """Reusable buffers for rendering P Gaussians into one view at a time."""
+    """Reusable buffers for rendering P Gaussians into one or more views."""
 
     def __init__(self, device="cuda", opts: capi.RasterOpts | None = None, pair_headroom: float = 1.25,
                  ppt_fwd: int | None = None, ppt_bwd: int | None = None):
@@ -44,11 +54,13 @@ class Rasterizer:
         self.opts_fwd = self._with_ppt(self.opts, ppt_fwd)
         self.opts_bwd = self._with_ppt(self.opts, ppt_bwd)
         self.headroom = pair_headroom
-        self.P_cap = -1
+        self.N_cap = -1
         self.M_cap = 0
         self.n_tiles = 0
         self.ws = None
+        self.rws = torch.empty(capi.dg_render_workspace_size(), dtype=torch.uint8, device=self.device)
         self.examined = None
+        self.blended = None
         self.mark = None  # optional callback(stage_name) after each stage, for event timing
 
     @staticmethod
@@ -63,11 +75,11 @@ class Rasterizer:
             self.mark(name)
 
     # ------------------------------------------------------------ buffers
-    def _ensure_prims(self, P):
-        if P <= self.P_cap:
+    def _ensure_records(self, N):
+        if N <= self.N_cap:
             return
         d = self.device
-        n = max(P, 1)
+        n = max(N, 1)
         self.feat = torch.empty((n, capi.FEAT_FLOATS), dtype=torch.float32, device=d)
         self.depth = torch.empty(n, dtype=torch.float32, device=d)
         self.radius = torch.empty(n, dtype=torch.int32, device=d)
@@ -76,11 +88,11 @@ class Rasterizer:
         self.grad2d = torch.empty((n, capi.FEAT_FLOATS), dtype=torch.float32, device=d)
         self.M_dev = torch.zeros(1, dtype=torch.int64, device=d)
         self.status = torch.zeros(1, dtype=torch.int32, device=d)
-        self.P_cap = P
+        self.N_cap = N
         self.ws = None
 
-    def _ensure_ws(self, P, M_cap, n_tiles):
-        need = capi.dg_bin_workspace_size(P, M_cap, n_tiles)
+    def _ensure_ws(self, P, n_views, M_cap):
+        need = capi.dg_bin_workspace_size(P, n_views, M_cap)
         if self.ws is None or self.ws.numel() < need:
             self.ws = torch.empty(need, dtype=torch.uint8, device=self.device)
         if M_cap > self.M_cap or not hasattr(self, "gid"):
@@ -93,65 +105,87 @@ class Rasterizer:
             self.n_tiles = n_tiles
 
     # ------------------------------------------------------------ passes
-    def forward(self, params: torch.Tensor, P: int, cam: capi.Camera, stream=None,
-                examined: bool = False) -> Frame:
+    def forward(self, params: torch.Tensor, P: int, cams, stream=None, examined: bool = False) -> Frame:
         """Project, bin, sort and composite P Gaussians of the planar
-        [59, stride] float32 tensor ``params`` into view ``cam``."""
+        [59, stride] float32 tensor ``params`` into one camera or a list of
+        cameras (at most 16)."""
         assert params.dtype == torch.float32 and params.shape[0] == NPARAM and params.stride(1) == 1
+        cams = [cams] if isinstance(cams, capi.Camera) else list(cams)
+        V = len(cams)
+        carr = capi.cameras(cams)
         stream = stream or torch.cuda.current_stream(self.device)
         B = self.opts.tile
-        W, H = cam.width, cam.height
-        n_tiles = ((W + B - 1) // B) * ((H + B - 1) // B)
-        self._ensure_prims(P)
+        sizes = [(c.width, c.height) for c in cams]
+        n_tiles = sum(((W + B - 1) // B) * ((H + B - 1) // B) for W, H in sizes)
+        npix = sum(W * H for W, H in sizes)
+        self._ensure_records(V * P)
         self._ensure_tiles(n_tiles)
         stride = params.stride(0)
-        capi.dg_project(params, stride, P, cam, self.opts, self.feat, self.depth, self.radius, self.tiles,
+        capi.dg_project(params, stride, P, carr, V, self.opts, self.feat, self.depth, self.radius, self.tiles,
                         self.clamp, stream)
         self._mark("project")
-        self._ensure_ws(P, max(self.M_cap, 1), n_tiles)
-        capi.dg_bin_count(self.depth, self.tiles, P, self.ws, self.ws.numel(), self.M_cap, n_tiles,
-                          self.M_dev, stream)
+        self._ensure_ws(P, V, max(self.M_cap, 1))
+        capi.dg_bin_count(self.depth, self.tiles, P, V, self.ws, self.ws.numel(), self.M_cap, self.M_dev, stream)
         self._mark("bin_count")
         stream.synchronize()
         M = int(self.M_dev.item())
         if M > self.M_cap:
-            self._ensure_ws(P, int(M * self.headroom) + 1024, n_tiles)
-            capi.dg_bin_count(self.depth, self.tiles, P, self.ws, self.ws.numel(), self.M_cap, n_tiles,
-                              self.M_dev, stream)
+            self._ensure_ws(P, V, int(M * self.headroom) + 1024)
+            capi.dg_bin_count(self.depth, self.tiles, P, V, self.ws, self.ws.numel(), self.M_cap, self.M_dev, stream)
         self._mark("host_sync")
-        capi.dg_bin_sort(self.feat, self.radius, P, cam, B, self.ws, self.ws.numel(), self.M_cap, self.gid,
+        capi.dg_bin_sort(self.feat, self.radius, P, carr, V, B, self.ws, self.ws.numel(), self.M_cap, self.gid,
                          self.ranges, self.status, stream)
         self._mark("bin_sort")
-        img = torch.empty((3, H, W), dtype=torch.float32, device=self.device)
-        T = torch.empty((H, W), dtype=torch.float32, device=self.device)
-        last = torch.empty((H, W), dtype=torch.int32, device=self.device)
+        img = torch.empty(3 * npix, dtype=torch.float32, device=self.device)
+        T = torch.empty(npix, dtype=torch.float32, device=self.device)
+        last = torch.empty(npix, dtype=torch.int32, device=self.device)
         ex = bl = None
         if examined:
-            ex = torch.empty((H, W), dtype=torch.int32, device=self.device)
-            bl = torch.empty((H, W), dtype=torch.int32, device=self.device)
-            self.examined = ex
-            self.blended = bl
-        capi.dg_render_fwd(self.feat, self.gid, self.ranges, cam, self.opts_fwd, img, T, last, ex, bl, stream)
+            ex = torch.empty(npix, dtype=torch.int32, device=self.device)
+            bl = torch.empty(npix, dtype=torch.int32, device=self.device)
+        capi.dg_render_fwd(self.feat, self.gid, self.ranges, carr, V, self.opts_fwd, img, T, last, ex, bl,
+                           self.rws, self.rws.numel(), stream)
         self._mark("render_fwd")
-        return Frame(P=P, cam=cam, img=img, T=T, last=last, M=M)
+        fr = Frame(P=P, cams=cams, img=img, T=T, last=last, M=M, flat_img=img, flat_T=T, flat_last=last)
+        off = 0
+        exs, bls = [], []
+        for W, H in sizes:
+            fr.images.append(img[3 * off: 3 * (off + W * H)].view(3, H, W))
+            fr.Ts.append(T[off: off + W * H].view(H, W))
+            fr.lasts.append(last[off: off + W * H].view(H, W))
+            if examined:
+                exs.append(ex[off: off + W * H].view(H, W))
+                bls.append(bl[off: off + W * H].view(H, W))
+            off += W * H
+        if V == 1:
+            fr.img, fr.T, fr.last = fr.images[0], fr.Ts[0], fr.lasts[0]
+        if examined:
+            self.examined = exs[0] if V == 1 else exs
+            self.blended = bls[0] if V == 1 else bls
+        return fr
 
     def backward(self, params: torch.Tensor, fr: Frame, dL_dimg: torch.Tensor, grads: torch.Tensor,
                  stream=None) -> None:
-        """Writes dL/dparams of the frame into the planar ``grads`` (same stride as params)."""
+        """Writes dL/dparams of the frame (summed over its views) into the
+        planar ``grads`` (same stride as params).  dL_dimg: the frame's image
+        layout ((3, H, W) for one view, the flat concatenation otherwise)."""
         stream = stream or torch.cuda.current_stream(self.device)
         assert dL_dimg.is_contiguous() and dL_dimg.dtype == torch.float32
-        capi.dg_render_bwd(self.feat, self.gid, self.ranges, fr.cam, self.opts_bwd, fr.T, fr.last, dL_dimg, fr.P,
-                           self.grad2d, stream)
+        assert dL_dimg.numel() == fr.flat_img.numel()
+        carr = capi.cameras(fr.cams)
+        V = len(fr.cams)
+        capi.dg_render_bwd(self.feat, self.gid, self.ranges, carr, V, self.opts_bwd, fr.flat_T, fr.flat_last,
+                           dL_dimg, V * fr.P, self.grad2d, self.rws, self.rws.numel(), stream)
         self._mark("render_bwd")
-        capi.dg_project_bwd(params, params.stride(0), fr.P, fr.cam, self.opts, self.radius, self.clamp,
+        capi.dg_project_bwd(params, params.stride(0), fr.P, carr, V, self.opts, self.radius, self.clamp,
                             self.grad2d, grads, stream)
         self._mark("project_bwd")
 
 
 class _RasterizeFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, params, rasterizer, cam):
-        fr = rasterizer.forward(params, params.shape[1], cam)
+    def forward(ctx, params, rasterizer, cams):
+        fr = rasterizer.forward(params, params.shape[1], cams)
         ctx.rasterizer = rasterizer
         ctx.frame = fr
         ctx.save_for_backward(params)
@@ -165,11 +199,12 @@ class _RasterizeFn(torch.autograd.Function):
         return grads, None, None
 
 
-def rasterize(params: torch.Tensor, rasterizer: Rasterizer, cam: capi.Camera) -> torch.Tensor:
-    """Differentiable render of the planar [59, P] float32 parameters into ``cam``.
+def rasterize(params: torch.Tensor, rasterizer: Rasterizer, cams) -> torch.Tensor:
+    """Differentiable render of the planar [59, P] float32 parameters into one
+    camera ((3, H, W) output) or a list of cameras (flat concatenation).
 
     The backward recomputes each pixel's transmittance from the stored final
     T and last contributor and returns dL/dparams with the same layout.  The
     rasterizer's buffers hold the state of the most recent call, so call
-    backward before rendering the next view with the same rasterizer."""
-    return _RasterizeFn.apply(params, rasterizer, cam)
+    backward before rendering the next batch with the same rasterizer."""
+    return _RasterizeFn.apply(params, rasterizer, cams)

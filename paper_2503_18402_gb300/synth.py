@@ -15,9 +15,13 @@ them with the shapes and parameter distributions of the workloads):
   * ``random_gaussians``: means U[-1,1]^3, log-scales N(-3, 0.5), random unit
     quaternions, opacity logit N(0, 1), SH coefficients N(0, 0.2^2).
   * ``textured_scene``: 90% of the Gaussians on 20 random planes and spheres
-    whose SH DC colour follows a seeded band-limited noise over the surface
-    coordinates, 10% on a uniform background shell of radius 12; the other
-    parameters are drawn as in ``random_gaussians``.
+    whose SH DC colour follows a seeded texture with a 1/f amplitude spectrum
+    (0.5 to 40 cycles per unit of surface coordinate, as natural images have)
+    over the surface coordinates, 10% on a uniform background shell of radius
+    12; the other parameters are drawn as in ``random_gaussians`` except the
+    log-scale mean, -4.5 instead of -3 (about 2 px instead of 10 px at
+    1237x822 for the 2M-Gaussian scene), so that the rendered views keep
+    real high-frequency content instead of a 10-px blur.
 """
 from __future__ import annotations
 
@@ -88,22 +92,29 @@ def target_image(width: int, height: int, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).uniform(0.0, 1.0, size=(3, height, width))
 
 
-def _band_noise(rng, n_waves=6):
-    k = rng.normal(0.0, 3.0, size=(n_waves, 2, 3))
+def _band_noise(rng, n_waves=32, f_lo=0.5, f_hi=40.0, std=0.25):
+    """Texture over surface coordinates with a natural-image-like 1/f
+    amplitude spectrum: plane waves with log-uniform spatial frequencies in
+    [f_lo, f_hi] cycles per unit, random directions and phases, amplitude
+    proportional to 1/f, scaled to the given standard deviation."""
+    f = np.exp(rng.uniform(math.log(f_lo), math.log(f_hi), size=(n_waves, 3)))
+    th = rng.uniform(0, 2 * math.pi, size=(n_waves, 3))
+    k = 2 * math.pi * f[:, None, :] * np.stack([np.cos(th), np.sin(th)], axis=1)  # (n, 2, 3)
     ph = rng.uniform(0, 2 * math.pi, size=(n_waves, 3))
-    amp = rng.uniform(0.2, 0.6, size=(n_waves, 3)) / n_waves ** 0.5
+    amp = 1.0 / f
+    amp *= std / np.sqrt(0.5 * (amp ** 2).sum(axis=0, keepdims=True))
 
-    def f(uv):
+    def tex(uv):
         out = np.zeros((uv.shape[0], 3))
         for w in range(n_waves):
             for ch in range(3):
                 out[:, ch] += amp[w, ch] * np.sin(uv @ k[w, :, ch] + ph[w, ch])
         return out
-    return f
+    return tex
 
 
 def textured_scene(n: int, seed: int, n_surfaces: int = 20, shell_radius: float = 12.0,
-                   dtype=np.float32) -> np.ndarray:
+                   log_scale_mean: float = -4.5, dtype=np.float32) -> np.ndarray:
     """(n, 59) Gaussians on textured planes/spheres plus a background shell."""
     rng = np.random.default_rng(seed)
     g = np.zeros((n, NPARAM), dtype=dtype)
@@ -130,16 +141,16 @@ def textured_scene(n: int, seed: int, n_surfaces: int = 20, shell_radius: float 
             ph = math.pi * uv[:, 1]
             d = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
             means[o:o + m] = centre + r * d
-        base = rng.uniform(0.2, 0.8, size=3)
-        dc[o:o + m] = base + tex(uv * 2.0)
+        base = rng.uniform(0.3, 0.7, size=3)
+        dc[o:o + m] = base + tex(uv)
         o += m
     d = rng.normal(size=(n_shell, 3))
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     means[o:] = shell_radius * d
-    sky = _band_noise(rng)
-    dc[o:] = 0.5 + sky(d[:, :2] * 2.0)
+    sky = _band_noise(rng, f_hi=20.0)
+    dc[o:] = 0.5 + sky(d[:, :2] * 4.0)
     g[:, 0:3] = means
-    g[:, 3:6] = rng.normal(-3.0, 0.5, size=(n, 3))
+    g[:, 3:6] = rng.normal(log_scale_mean, 0.5, size=(n, 3))
     g[o:, 3:6] += math.log(shell_radius / 4.0)  # shell Gaussians scaled with distance
     q = rng.normal(size=(n, 4))
     g[:, 6:10] = q / np.linalg.norm(q, axis=1, keepdims=True)

@@ -57,6 +57,10 @@ class TrainConfig:
     lr_opacity: float = 0.025
     lr_scale: float = 0.005
     lr_rot: float = 0.001
+    # 3DGS prunes "big points" (screen radius > 20 px, scale > 0.1 extent) after
+    # the first opacity reset; off by default here because the synthetic ground
+    # truth's Gaussians already have ~30 px radii at full resolution
+    big_point_prune: bool = False
     seed: int = 0
 
 
@@ -156,7 +160,8 @@ class Trainer:
         capi.dg_loss_l1(fr.img, self._target(j, r, h, w), n, self.dL, self.loss, self.lws, self.lws.numel(), self.stream)
         self.rz.backward(params, fr, self.dL[:n].view(3, h, w), self.grads[:, :P], self.stream)
         if k < cfg.densify_until:
-            capi.dg_densify_stats(self.rz.grad2d, self.rz.radius, P, w, h, self.acc, self.den, self.maxr, self.stream)
+            capi.dg_densify_stats(self.rz.grad2d, self.rz.radius, P, cam, 1, self.acc, self.den, self.maxr,
+                                  self.stream)
         lr = [lr_pos] * 3 + [cfg.lr_scale] * 3 + [cfg.lr_rot] * 4 + [cfg.lr_opacity] + [cfg.lr_dc] * 3 + \
              [cfg.lr_rest] * 45
         capi.dg_adam_step(b["p"], self.grads, b["m"], b["v"], self.cap, P, lr, 0.9, 0.999, 1e-15, k + 1, self.stream)
@@ -176,7 +181,7 @@ class Trainer:
         need = capi.dg_densify_workspace_size(P)
         if self.dws is None or self.dws.numel() < need:
             self.dws = torch.empty(int(need * 1.2) + 1024, dtype=torch.uint8, device=self.dev)
-        big = k > cfg.opacity_reset_every
+        big = cfg.big_point_prune and k > cfg.opacity_reset_every
         opts = capi.densify_opts(cfg.grad_thresh, cfg.min_opacity, cfg.percent_dense, cfg.extent,
                                  20.0 if big else 0.0, 0.1 * cfg.extent if big else 0.0)
         capi.dg_densify_mark(b["p"], self.cap, P, self.acc, self.den, self.maxr, opts, self.dws, self.dws.numel(),

@@ -52,15 +52,23 @@ def test_binding_covers_every_export():
 def test_host_only_calls_without_gpu():
     from paper_2503_18402_gb300 import capi
     assert capi.dg_abi_version() == 1
-    assert capi.dg_bin_workspace_size(1000, 5000, 16) > 5000 * 16
-    assert capi.dg_bin_workspace_size(-1, 0, 1) == 0
+    assert capi.dg_bin_workspace_size(1000, 1, 5000) > 5000 * 16
+    assert capi.dg_bin_workspace_size(1000, 4, 5000) > capi.dg_bin_workspace_size(1000, 1, 5000)
+    assert capi.dg_bin_workspace_size(-1, 1, 0) == 0
+    assert capi.dg_bin_workspace_size(10, 17, 0) == 0  # more views than one call takes
+    assert capi.dg_render_workspace_size() >= 4
     assert capi.dg_loss_workspace_size(100) >= 4
     # argument validation happens on the host before any launch
     opts = capi.raster_opts(sh_degree=7)
     cam = capi.camera([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 4], 50, 50, 32, 32, 64, 64)
     with pytest.raises(capi.DashGSError) as e:
-        capi.dg_project(1 << 20, 8, 8, cam, opts, 1 << 21, 1 << 22, 1 << 23, 1 << 24, 1 << 25)
+        capi.dg_project(1 << 20, 8, 8, cam, 1, opts, 1 << 21, 1 << 22, 1 << 23, 1 << 24, 1 << 25)
     assert e.value.status == capi.DG_ERR_ARG and "sh_degree" in capi.dg_last_error()
     with pytest.raises(capi.DashGSError) as e:
-        capi.dg_render_fwd(1 << 20, 1 << 21, 1 << 22, cam, capi.raster_opts(tile=12), 1, 2, 3, None)
+        capi.dg_render_fwd(1 << 20, 1 << 21, 1 << 22, cam, 1, capi.raster_opts(tile=12), 1, 2, 3, None, None,
+                           1 << 26, 256)
     assert "tile" in str(e.value)
+    with pytest.raises(capi.DashGSError) as e:
+        capi.dg_project(1 << 20, 8, 8, [cam] * 17, 17, capi.raster_opts(), 1 << 21, 1 << 22, 1 << 23, 1 << 24,
+                        1 << 25)
+    assert "n_views" in str(e.value)

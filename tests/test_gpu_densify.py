@@ -91,7 +91,8 @@ def test_densify_stats_matches_oracle():
     den = rng.integers(0, 5, size=P).astype(np.float32)
     mr = rng.integers(0, 20, size=P).astype(np.float32)
     t = [torch.from_numpy(x.copy()).cuda() for x in (g2, rad, acc, den, mr)]
-    capi.dg_densify_stats(t[0], t[1], P, W, H, t[2], t[3], t[4])
+    cam = capi.camera([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], 100, 100, W / 2, H / 2, W, H)
+    capi.dg_densify_stats(t[0], t[1], P, cam, 1, t[2], t[3], t[4])
     torch.cuda.synchronize()
     oa, od, om = D.stats_update(acc.astype(np.float64), den.astype(np.float64), mr.astype(np.float64),
                                 g2.astype(np.float64), rad, W, H)

@@ -261,13 +261,13 @@ def test_pair_capacity_overflow_reports_status():
     P = g.shape[0]
     M = fr.M
     small = M // 2
-    ws = torch.empty(capi.dg_bin_workspace_size(P, small, rz.n_tiles), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(capi.dg_bin_workspace_size(P, 1, small), dtype=torch.uint8, device="cuda")
     gid = torch.full((small,), -7, dtype=torch.int32, device="cuda")
     ranges = torch.full((rz.n_tiles, 2), 5, dtype=torch.int32, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     Mdev = torch.zeros(1, dtype=torch.int64, device="cuda")
-    capi.dg_bin_count(rz.depth, rz.tiles, P, ws, ws.numel(), small, rz.n_tiles, Mdev)
-    capi.dg_bin_sort(rz.feat, rz.radius, P, gcam, 16, ws, ws.numel(), small, gid, ranges, status)
+    capi.dg_bin_count(rz.depth, rz.tiles, P, 1, ws, ws.numel(), small, Mdev)
+    capi.dg_bin_sort(rz.feat, rz.radius, P, gcam, 1, 16, ws, ws.numel(), small, gid, ranges, status)
     torch.cuda.synchronize()
     assert int(Mdev.item()) == M
     assert int(status.item()) == capi.DG_ERR_CAPACITY
@@ -279,10 +279,10 @@ def test_host_side_argument_errors():
     cam = G.gpu_camera(synth.camera_cfg0(64, 64, 4.0))
     t = torch.zeros((59, 4), device="cuda")
     with pytest.raises(capi.DashGSError) as e:
-        capi.dg_project(t, 4, 4, cam, opts, t, t, t, t, t)
+        capi.dg_project(t, 4, 4, cam, 1, opts, t, t, t, t, t)
     assert e.value.status == capi.DG_ERR_ARG and "sh_degree" in str(e.value)
     with pytest.raises(capi.DashGSError):
-        capi.dg_project(t, 2, 4, cam, capi.raster_opts(), t, t, t, t, t)  # stride < P
+        capi.dg_project(t, 2, 4, cam, 1, capi.raster_opts(), t, t, t, t, t)  # stride < P
 
 
 # ---------------------------------------------------------------- loss, Adam
@@ -391,3 +391,57 @@ def test_fullsize_backward_on_sampled_tiles(fullsize):
     assert ok, (worst, nbad)
     touched = np.abs(og2).sum(1) > 0
     assert touched.sum() > 1000
+
+
+# ---------------------------------------------------------------- several views per call
+def test_batched_views_match_single_view_renders():
+    g = synth.random_gaussians(3000, 31)
+    g[:, 3:6] += 0.3
+    sizes = [(64, 64), (72, 40), (130, 99)]
+    cams = []
+    for i, (W, H) in enumerate(sizes):
+        c = synth.camera_cfg0(W, H, 4.0 + 0.5 * i)
+        cams.append(c)
+    opts = capi.raster_opts(bg=(0.1, 0.3, 0.2))
+    params = G.gpu_params(g)
+    P = g.shape[0]
+    gcams = [G.gpu_camera(c) for c in cams]
+    rzb = Rasterizer("cuda", opts)
+    frb = rzb.forward(params, P, gcams, examined=True)
+    rng = np.random.default_rng(3)
+    dLs = [(rng.normal(size=(3, H, W)) / (3 * 64 * 64)).astype(np.float32) for W, H in sizes]
+    dL = torch.from_numpy(np.concatenate([d.reshape(-1) for d in dLs])).cuda()
+    gb = torch.empty_like(params)
+    rzb.backward(params, frb, dL, gb)
+    torch.cuda.synchronize()
+    gsum = np.zeros((59, P))
+    for v, (c, (W, H)) in enumerate(zip(gcams, sizes)):
+        rz = Rasterizer("cuda", opts)
+        fr = rz.forward(params, P, c, examined=True)
+        gv = torch.empty_like(params)
+        rz.backward(params, fr, torch.from_numpy(dLs[v]).cuda(), gv)
+        torch.cuda.synchronize()
+        # the batched render of a view is the single-view render, bit for bit
+        np.testing.assert_array_equal(G.np_(frb.images[v]), G.np_(fr.img))
+        np.testing.assert_array_equal(G.np_(frb.Ts[v]), G.np_(fr.T))
+        np.testing.assert_array_equal(G.np_(frb.lasts[v]), G.np_(fr.last))
+        np.testing.assert_array_equal(G.np_(rzb.blended[v]), G.np_(rz.blended))
+        gsum += G.np_(gv)
+    ok, worst, nbad = G.grad_close(G.np_(gb).T, gsum.T)
+    assert ok, (worst, nbad)
+    # and each batched view against the oracle, fed the batch's own FP32
+    # records (payload v*P + i) and its pair list; tile ranges of view v
+    # start after the tiles of views 0..v-1
+    k = oracle.consts()
+    feat = G.np_(rzb.feat[: len(sizes) * P]).astype(np.float64)[:, :9]
+    gid = G.np_(rzb.gid[: frb.M]).view(np.uint32)
+    ranges = G.np_(rzb.ranges[: rzb.n_tiles]).view(np.uint32)
+    t0 = 0
+    for v, (W, H) in enumerate(sizes):
+        nt = ((W + 15) // 16) * ((H + 15) // 16)
+        orf = oracle.render_fwd(feat, W, H, 16, gid, ranges[t0: t0 + nt], G.f32((0.1, 0.3, 0.2)), k)
+        t0 += nt
+        assert np.abs(G.np_(frb.images[v]) - orf["img"]).max() <= 1e-5
+        assert np.abs(G.np_(frb.Ts[v]) - orf["T"]).max() <= 1e-5
+        np.testing.assert_array_equal(G.np_(frb.lasts[v]), orf["last"])
+        np.testing.assert_array_equal(G.np_(rzb.blended[v]), orf["blended"])
