@@ -47,15 +47,20 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-gauss", type=int, default=N_GAUSS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--unfused-adam", action="store_true",
+                    help="projection adjoint and Adam as two kernels (default: fused)")
     ap.add_argument("--cpu-frac", type=float, default=0.125,
                     help="area/Gaussian fraction of one view timed for the CPU baseline")
     return ap.parse_args()
 
 
-def config(args, n_gauss):
+def config(args, n_gauss, shape=None):
     return {"workload": f"textured-{n_gauss // 1000}k-gaussians-{W_FULL}x{H_FULL}-1view-fp32",
             "n_gaussians": n_gauss, "width": W_FULL, "height": H_FULL, "views_per_step": 1,
-            "tile": 16, "sh_degree": 3, "step": "project+bin+render_fwd+L1+render_bwd+project_bwd+adam",
+            "tile": shape.tile if shape else 16, "render_shape": shape.label() if shape else None,
+            "sh_degree": 3, "loss": "0.8 L1 + 0.2 D-SSIM",
+            "step": "project+bin+render_fwd+loss+render_bwd+project_bwd+adam",
+            "adjoint_adam": "two kernels" if args.unfused_adam else "fused",
             "l2": "working set 1.9 GB > L2 (no flush)", "parallelism": f"replicas{args.gpus}"}
 
 
@@ -115,6 +120,7 @@ def run_ours(args):
     import torch.distributed as dist
 
     from paper_2503_18402_gb300 import capi
+    from paper_2503_18402_gb300.autotune import CANDIDATES, RenderTuner
     from paper_2503_18402_gb300.raster import Rasterizer, make_camera
 
     world = args.gpus
@@ -144,11 +150,55 @@ def run_ours(args):
     stride = params.stride(0)
     extent = 5.0
     lr = [1.6e-4 * extent] * 3 + [0.005] * 3 + [0.001] * 4 + [0.025] + [0.0025] * 3 + [0.0025 / 20] * 45
-    n_pix = 3 * H_FULL * W_FULL
     dL = torch.empty((3, H_FULL, W_FULL), dtype=torch.float32, device=dev)
-    loss = torch.zeros(1, dtype=torch.float32, device=dev)
-    lws = torch.empty(capi.dg_loss_workspace_size(n_pix), dtype=torch.uint8, device=dev)
+    loss = torch.zeros(2, dtype=torch.float32, device=dev)
+    sws = torch.empty(capi.dg_ssim_workspace_size([(W_FULL, H_FULL)]), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    adam_t = [0]
+
+    def step_with(r, i, tgt=None, mark=None):
+        j = i % N_VIEWS
+        r.mark = mark
+        if mark:
+            mark("start")
+        fr = r.forward(params, P, gcams[j])
+        capi.dg_loss_l1_dssim(fr.img, targets[j] if tgt is None else tgt, [(W_FULL, H_FULL)], 0.2, dL, loss, sws,
+                              sws.numel(), stream)
+        if mark:
+            mark("loss")
+        r.backward_render(fr, dL, stream)
+        adam_t[0] += 1
+        if args.unfused_adam:
+            capi.dg_project_bwd(params, stride, P, gcams[j], 1, r.opts, r.radius, r.clamp, r.grad2d, grads, stream)
+            if mark:
+                mark("project_bwd")
+            capi.dg_adam_step(params, grads, m, v, stride, P, lr, 0.9, 0.999, 1e-15, adam_t[0], stream)
+            if mark:
+                mark("adam")
+        else:
+            r.project_bwd_adam(params, stride, fr, m, v, lr, adam_t[0], stream=stream)
+        return fr
+
+    # launch-shape autotuning: time each candidate on a few steps, keep the fastest
+    tuner = RenderTuner(dev, opts)
+    tune_ms = {}
+    for shape in CANDIDATES:
+        r = tuner.rasterizer(shape)
+        for i in range(2):
+            step_with(r, i)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(4):
+            step_with(r, 2 + i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tune_ms[shape] = e0.elapsed_time(e1) / 4
+    shape = min(tune_ms, key=tune_ms.get)
+    rz = tuner.rasterizer(shape)
+    # restart the optimisation from the same state for the timed run
+    params.copy_(torch.from_numpy(np.ascontiguousarray(model.T)).to(dev))
+    m.zero_(); v.zero_(); adam_t[0] = 0
 
     # algorithmic work per view: examined entries (forward) and back-traversed entries
     E_f, E_b, M_tot = [], [], []
@@ -166,23 +216,8 @@ def run_ours(args):
         e.record(stream)
         events.append((name, e))
 
-    adam_t = [0]
-
     def step(i, tgt=None, stage_events=False):
-        j = i % N_VIEWS
-        rz.mark = mark if stage_events else None
-        if stage_events:
-            mark("start")
-        fr = rz.forward(params, P, gcams[j])
-        capi.dg_loss_l1(fr.img, targets[j] if tgt is None else tgt, n_pix, dL, loss, lws, lws.numel(), stream)
-        if stage_events:
-            mark("loss")
-        rz.backward(params, fr, dL, grads)
-        adam_t[0] += 1
-        capi.dg_adam_step(params, grads, m, v, stride, P, lr, 0.9, 0.999, 1e-15, adam_t[0], stream)
-        if stage_events:
-            mark("adam")
-        return fr
+        return step_with(rz, i, tgt, mark if stage_events else None)
 
     for i in range(args.warmup):
         step(i)
@@ -231,7 +266,7 @@ def run_ours(args):
     for i in range(2):
         tgt_dev.copy_(pinned[i % N_VIEWS], non_blocking=True)
         step(i, tgt=tgt_dev)
-        loss.item()
+        loss[1].item()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -239,7 +274,7 @@ def run_ours(args):
     for i in range(args.steps):
         tgt_dev.copy_(pinned[i % N_VIEWS], non_blocking=True)
         step(i, tgt=tgt_dev)
-        float(loss.item())
+        float(loss[1].item())
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - e0) * 1e3
     if world > 1:
@@ -254,7 +289,8 @@ def run_ours(args):
         "value": round(ms_per_view, 4), "unit": "ms/view", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded textured scene)",
-        "config": config(args, P), "impl": "ours",
+        "config": config(args, P, shape), "impl": "ours",
+        "autotune_ms_per_step": {s.label(): round(t, 4) for s, t in tune_ms.items()},
     }
     tot = sum(stage_ms.values())
     stages = {k: {"ms": round(v / args.steps, 4), "share": round(v / tot, 4)} for k, v in stage_ms.items()}
@@ -262,7 +298,8 @@ def run_ours(args):
     pf = sum(E_f) / len(E_f)
     pb = sum(E_b) / len(E_b)
     work = {"render_fwd": ("alu", pb * FLOPS_FWD), "render_bwd": ("alu", pb * FLOPS_BWD),
-            "project": ("hbm", P * 297.0), "project_bwd": ("hbm", P * 525.0), "adam": ("hbm", P * 1652.0)}
+            "project": ("hbm", P * 297.0), "project_bwd": ("hbm", P * 525.0), "adam": ("hbm", P * 1652.0),
+            "project_bwd_adam": ("hbm", P * 1469.0)}
     dom = max((k for k in stages if k in work), key=lambda k: stages[k]["ms"])
     kind, units = work[dom]
     dur_s = stages[dom]["ms"] * 1e-3
@@ -285,7 +322,8 @@ def run_ours(args):
                            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s"}
     out["work"] = {"pairs_per_view": int(sum(M_tot) / len(M_tot)), "examined_per_view": int(pf),
                    "blended_per_view": int(pb)}
-    out["fwd_bwd_ms_per_view"] = round(sum(stages[k]["ms"] for k in stages if k not in ("adam", "loss")), 4)
+    out["fwd_bwd_ms_per_view"] = round(sum(stages[k]["ms"] for k in stages
+                                           if k not in ("adam", "loss", "project_bwd_adam")), 4)
     out["e2e"] = {"value": round(e2e_ms / views_total, 4), "unit": "ms/view",
                   "h2d_bytes_per_step": int(targets[0].numel() * 4), "d2h_bytes_per_step": 4 + 8}
     out["gpu_launches"] = int(launches)

@@ -81,8 +81,15 @@ typedef struct dg_camera {
  * near_plane are culled (0.2); eps2d: dilation added to the 2D covariance
  * diagonal, px^2 (0.3); bg: background colour composited with the final
  * transmittance; pixels_per_thread: pixels each render thread owns (1, 2 or
- * 4 with tile 16; 0 = the library's default per pass).  It changes the launch
- * shape only, not the result beyond float summation order. */
+ * 4 with tile 16; 0 = the library's default per pass); split_len: list
+ * splitting of the render passes: a tile whose sorted list is longer than L
+ * entries is composited as ceil(n/L) chunks in parallel (Eq. 1 composes over
+ * chunks through the transmittance product); 0 = automatic (split when the
+ * batch has fewer tiles than twice the resident CTAs, L = max(64, M / resident
+ * CTAs)), > 0 = always split with that L (raised where the workspace needs
+ * it), < 0 = never split.
+ * pixels_per_thread and split_len change the launch shape only, not the
+ * result beyond float rounding order. */
 typedef struct dg_raster_opts {
     int32_t tile;
     int32_t sh_degree;
@@ -90,6 +97,7 @@ typedef struct dg_raster_opts {
     float eps2d;
     float bg[3];
     int32_t pixels_per_thread;
+    int32_t split_len;
 } dg_raster_opts;
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
@@ -160,8 +168,13 @@ DG_API dg_status dg_bin_sort(const float* feat, const int32_t* radius, int64_t P
                       uint32_t* ranges, int32_t* status, dg_stream stream);
 
 /* ---------------------------------------------------------------------- */
-/* Render workspace (a work counter of the persistent launch): bytes. */
-DG_API size_t dg_render_workspace_size(void);
+/* Render workspace for these cameras and options: work counters of the
+ * persistent launches and, unless opts->split_len < 0, the split plan and
+ * per-pixel chunk state (about 40 MB plus 40 bytes per tile).  Returns 0 for
+ * invalid arguments.  The workspace must be 256-byte aligned.  dg_render_bwd
+ * must get the workspace, cameras, tile and split_len of the dg_render_fwd
+ * of the same batch, unmodified in between. */
+DG_API size_t dg_render_workspace_size(const dg_camera* cams, int32_t n_views, const dg_raster_opts* opts);
 
 /* Forward compositing, Eq. 1: per pixel, front to back over its tile's list,
  * C = sum_i T_i alpha_i c_i + T_N bg.  One persistent launch covers every
@@ -198,6 +211,18 @@ DG_API dg_status dg_project_bwd(const float* params, int64_t stride, int64_t P, 
                          int32_t n_views, const dg_raster_opts* opts, const int32_t* radius, const uint8_t* clamp,
                          const float* grad2d, float* grads, dg_stream stream);
 
+/* dg_project_bwd fused with dg_adam_step: the gradient of each parameter row
+ * goes straight into the Adam update of that row (same arithmetic and result
+ * as the two calls in sequence), so it is never stored and reloaded and the
+ * parameters are read once (1.47 kB instead of 2.18 kB of HBM traffic per
+ * Gaussian).  grads: nullable; when given, the gradient is also written there.
+ * params, m, v: planar [59][stride], updated in place; lr: host float[59]. */
+DG_API dg_status dg_project_bwd_adam(float* params, int64_t stride, int64_t P, const dg_camera* cams,
+                                     int32_t n_views, const dg_raster_opts* opts, const int32_t* radius,
+                                     const uint8_t* clamp, const float* grad2d, float* grads, float* m, float* v,
+                                     const float* lr, float beta1, float beta2, float eps, int64_t step,
+                                     dg_stream stream);
+
 /* ---------------------------------------------------------------------- */
 /* L1 photometric loss of the 3DGS backbone the paper keeps (Sec. 5):
  * loss = mean |img - target| over n values; dL_dimg = sign(img - target)/n
@@ -206,6 +231,22 @@ DG_API dg_status dg_project_bwd(const float* params, int64_t stride, int64_t P, 
 DG_API size_t dg_loss_workspace_size(int64_t n);
 DG_API dg_status dg_loss_l1(const float* img, const float* target, int64_t n, float* dL_dimg,
                      float* loss, void* ws, size_t ws_bytes, dg_stream stream);
+
+/* Training loss of the 3DGS backbone the paper keeps unchanged (Sec. 5):
+ * L_v = (1 - lambda) mean|img - target| + lambda (1 - SSIM) per view, SSIM of
+ * Wang et al. 2004 (11 x 11 Gaussian window, sigma 1.5, C1 = 0.01^2,
+ * C2 = 0.03^2, zero padding, mean over pixels and channels); the backbone
+ * uses lambda = 0.2.
+ * In:  img, target: n_views planar images [3][H_v][W_v] concatenated (the
+ *      render layout); wh: host int32 [n_views][2] = (W_v, H_v).
+ * Out: dL_dimg (same layout) = gradient of the mean over views of L_v;
+ *      loss: device float32 [n_views + 1] = L_0 .. L_{n-1}, then the mean.
+ * ws: dg_ssim_workspace_size(wh, n_views) bytes (36 bytes per pixel plus
+ * per-block sums); 0 is returned for invalid sizes. */
+DG_API size_t dg_ssim_workspace_size(const int32_t* wh, int32_t n_views);
+DG_API dg_status dg_loss_l1_dssim(const float* img, const float* target, const int32_t* wh, int32_t n_views,
+                                  float lambda, float* dL_dimg, float* loss, void* ws, size_t ws_bytes,
+                                  dg_stream stream);
 
 /* Mean squared error of two arrays (held-out PSNR = -10 log10(mse) for images
  * in [0, 1]; Sec. 5 "Metrics").  ws: dg_loss_workspace_size(n) bytes. */

@@ -24,8 +24,8 @@ DG_OK, DG_ERR_ARG, DG_ERR_CAPACITY, DG_ERR_TIMEOUT, DG_ERR_CUDA = 0, -1, -2, -3,
 
 MAX_VIEWS = 16
 EXPORTS = ("dg_last_error", "dg_abi_version", "dg_kernel_launches", "dg_project", "dg_bin_workspace_size", "dg_bin_count",
-           "dg_bin_sort", "dg_render_workspace_size", "dg_render_fwd", "dg_render_bwd", "dg_project_bwd",
-           "dg_loss_workspace_size",
+           "dg_bin_sort", "dg_render_workspace_size", "dg_render_fwd", "dg_render_bwd", "dg_project_bwd", "dg_project_bwd_adam",
+           "dg_loss_workspace_size", "dg_ssim_workspace_size", "dg_loss_l1_dssim",
            "dg_loss_l1", "dg_loss_l1_noalloc", "dg_adam_step", "dg_spectrum_workspace_size",
            "dg_spectrum_accumulate", "dg_spectrum_finalize", "dg_downsample_area", "dg_schedule_init",
            "dg_schedule_step", "dg_schedule_densify", "dg_densify_stats", "dg_densify_workspace_size",
@@ -47,7 +47,8 @@ class Camera(ctypes.Structure):
 
 class RasterOpts(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("near_plane", ctypes.c_float),
-                ("eps2d", ctypes.c_float), ("bg", ctypes.c_float * 3), ("pixels_per_thread", ctypes.c_int32)]
+                ("eps2d", ctypes.c_float), ("bg", ctypes.c_float * 3), ("pixels_per_thread", ctypes.c_int32),
+                ("split_len", ctypes.c_int32)]
 
 
 SCHED_MAX_LEVELS = 64
@@ -98,11 +99,12 @@ def camera(viewmat, fx, fy, cx, cy, width, height) -> Camera:
 
 
 def raster_opts(tile=16, sh_degree=3, near_plane=0.2, eps2d=0.3, bg=(0.0, 0.0, 0.0),
-                pixels_per_thread=0) -> RasterOpts:
+                pixels_per_thread=0, split_len=0) -> RasterOpts:
     o = RasterOpts()
     o.tile, o.sh_degree, o.near_plane, o.eps2d = int(tile), int(sh_degree), float(near_plane), float(eps2d)
     o.bg[:] = [float(b) for b in bg]
     o.pixels_per_thread = int(pixels_per_thread)
+    o.split_len = int(split_len)
     return o
 
 
@@ -123,10 +125,14 @@ _SIGS = {
     "dg_bin_workspace_size": ([_I64, _I32, _I64], _SZ),
     "dg_bin_count": ([_P, _P, _I64, _I32, _P, _SZ, _I64, _P, _P], _ST),
     "dg_bin_sort": ([_P, _P, _I64, _CAM, _I32, _I32, _P, _SZ, _I64, _P, _P, _P, _P], _ST),
-    "dg_render_workspace_size": ([], _SZ),
+    "dg_render_workspace_size": ([_CAM, _I32, _OPT], _SZ),
     "dg_render_fwd": ([_P, _P, _P, _CAM, _I32, _OPT, _P, _P, _P, _P, _P, _P, _SZ, _P], _ST),
     "dg_render_bwd": ([_P, _P, _P, _CAM, _I32, _OPT, _P, _P, _P, _I64, _P, _P, _SZ, _P], _ST),
     "dg_project_bwd": ([_P, _I64, _I64, _CAM, _I32, _OPT, _P, _P, _P, _P, _P], _ST),
+    "dg_project_bwd_adam": ([_P, _I64, _I64, _CAM, _I32, _OPT, _P, _P, _P, _P, _P, _P, _P, ctypes.c_float,
+                             ctypes.c_float, ctypes.c_float, _I64, _P], _ST),
+    "dg_ssim_workspace_size": ([_P, _I32], _SZ),
+    "dg_loss_l1_dssim": ([_P, _P, _P, _I32, ctypes.c_float, _P, _P, _P, _SZ, _P], _ST),
     "dg_loss_workspace_size": ([_I64], _SZ),
     "dg_loss_l1": ([_P, _P, _I64, _P, _P, _P, _SZ, _P], _ST),
     "dg_loss_l1_noalloc": ([_P, _P, _I64, _P, _P, _P], _ST),
@@ -223,8 +229,8 @@ def dg_bin_sort(feat, radius, P, cams, n_views, tile, ws, ws_bytes, M_cap, gid, 
                             _a(ranges), _a(status), _s(stream)))
 
 
-def dg_render_workspace_size() -> int:
-    return _lib.dg_render_workspace_size()
+def dg_render_workspace_size(cams, n_views, opts) -> int:
+    return _lib.dg_render_workspace_size(_c(cams), n_views, ctypes.byref(opts))
 
 
 def dg_render_fwd(feat, gid, ranges, cams, n_views, opts, img, T_final, last, examined, blended, ws, ws_bytes,
@@ -244,12 +250,37 @@ def dg_project_bwd(params, stride, P, cams, n_views, opts, radius, clamp, grad2d
                                _a(grad2d), _a(grads), _s(stream)))
 
 
+def dg_project_bwd_adam(params, stride, P, cams, n_views, opts, radius, clamp, grad2d, grads, m, v, lr, beta1,
+                        beta2, eps, step, stream=None):
+    lr_arr = (ctypes.c_float * NPARAM)(*[float(x) for x in lr])
+    _check(_lib.dg_project_bwd_adam(_a(params), stride, P, _c(cams), n_views, ctypes.byref(opts), _a(radius),
+                                    _a(clamp), _a(grad2d), _a(grads), _a(m), _a(v), ctypes.cast(lr_arr, ctypes.c_void_p), beta1,
+                                    beta2, eps, step,
+                                    _s(stream)))
+
+
 def dg_loss_workspace_size(n) -> int:
     return _lib.dg_loss_workspace_size(n)
 
 
 def dg_loss_l1(img, target, n, dL_dimg, loss, ws, ws_bytes, stream=None):
     _check(_lib.dg_loss_l1(_a(img), _a(target), n, _a(dL_dimg), _a(loss), _a(ws), ws_bytes, _s(stream)))
+
+
+def _wh(sizes):
+    """Host int32 [n][2] array of (W, H) pairs."""
+    flat = [int(x) for wh in sizes for x in wh]
+    return (ctypes.c_int32 * len(flat))(*flat)
+
+
+def dg_ssim_workspace_size(sizes) -> int:
+    return _lib.dg_ssim_workspace_size(_wh(sizes), len(sizes))
+
+
+def dg_loss_l1_dssim(img, target, sizes, lam, dL_dimg, loss, ws, ws_bytes, stream=None):
+    """(1 - lam) L1 + lam (1 - SSIM) per view; sizes: list of (W, H)."""
+    _check(_lib.dg_loss_l1_dssim(_a(img), _a(target), _wh(sizes), len(sizes), float(lam), _a(dL_dimg), _a(loss),
+                                 _a(ws), ws_bytes, _s(stream)))
 
 
 def dg_loss_l1_noalloc(img, target, n, dL_dimg, loss, stream=None):

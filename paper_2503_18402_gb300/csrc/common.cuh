@@ -61,6 +61,22 @@ __device__ inline Rect tile_rect(float u, float v, int r, int B, int TX, int TY)
     return q;
 }
 
+// Adam hyper-parameters of one step: per-row learning rate, betas, bias
+// corrections 1 - b1^t and sqrt(1 - b2^t), epsilon.
+struct AdamHp {
+    float lr[DG_NPARAM];
+    float b1, b2, bc1, bc2_sqrt, eps;
+};
+
+// One Adam update of a scalar parameter (shared by the standalone and the fused
+// kernels so that both give the same bits).
+__device__ __forceinline__ void adam_update(float& p, float& m, float& v, float g, float lr, const AdamHp& h)
+{
+    m = fmaf(h.b1, m, (1.f - h.b1) * g);
+    v = fmaf(h.b2, v, (1.f - h.b2) * (g * g));
+    p -= (lr / h.bc1) * m / (sqrtf(v) / h.bc2_sqrt + h.eps);
+}
+
 }  // namespace dg
 
 // Host-side error reporting shared by the C-ABI entry points.
@@ -68,3 +84,5 @@ void dg_set_error(const char* fmt, ...);
 // Counts kernel launches issued by this library (read by dg_kernel_launches).
 void dg_note_launch(int n = 1);
 dg_status dg_check_launch(const char* what);
+// Adam hyper-parameters of step `step` (bias corrections in FP64, rounded once).
+dg::AdamHp dg_adam_hp(const float* lr, float beta1, float beta2, float eps, int64_t step);

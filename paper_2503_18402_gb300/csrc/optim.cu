@@ -83,21 +83,16 @@ __global__ void k_opacity_reset(float* __restrict__ prm, float* __restrict__ m, 
     v[o] = 0.f;
 }
 
-struct AdamRow {
-    float lr[DG_NPARAM];
-};
-
 // One thread per 4 consecutive Gaussians of one parameter row (float4 when the
 // row start is 16-byte aligned, scalar otherwise).
 __global__ void __launch_bounds__(256)
 k_adam(float* __restrict__ prm, const float* __restrict__ grd, float* __restrict__ m,
-       float* __restrict__ v, long long stride, long long P, AdamRow lr, float b1, float b2,
-       float bc1, float bc2_sqrt, float eps)
+       float* __restrict__ v, long long stride, long long P, AdamHp hp)
 {
     const int row = blockIdx.y;
     const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (i0 >= P) return;
-    const float step = lr.lr[row] / bc1;
+    const float lr = hp.lr[row];
     const long long o = (long long)row * stride + i0;
     const bool vec = ((o & 3) == 0) && (i0 + 3 < P) && ((((uintptr_t)prm) & 15u) == 0) &&
                      ((((uintptr_t)grd) & 15u) == 0) && ((((uintptr_t)m) & 15u) == 0) &&
@@ -107,28 +102,35 @@ k_adam(float* __restrict__ prm, const float* __restrict__ grd, float* __restrict
         float4 mm = *(float4*)(m + o), vv = *(float4*)(v + o);
         float* pp = &p.x; const float* gg = &g.x; float* mp = &mm.x; float* vp = &vv.x;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            mp[c] = b1 * mp[c] + (1.f - b1) * gg[c];
-            vp[c] = b2 * vp[c] + (1.f - b2) * gg[c] * gg[c];
-            pp[c] -= step * mp[c] / (sqrtf(vp[c]) / bc2_sqrt + eps);
-        }
+        for (int c = 0; c < 4; ++c) adam_update(pp[c], mp[c], vp[c], gg[c], lr, hp);
         *(float4*)(prm + o) = p;
         *(float4*)(m + o) = mm;
         *(float4*)(v + o) = vv;
     } else {
         for (int c = 0; c < 4 && i0 + c < P; ++c) {
             const long long k = o + c;
-            const float gc = grd[k];
-            const float mc = b1 * m[k] + (1.f - b1) * gc;
-            const float vc = b2 * v[k] + (1.f - b2) * gc * gc;
+            float pc = prm[k], mc = m[k], vc = v[k];
+            adam_update(pc, mc, vc, grd[k], lr, hp);
+            prm[k] = pc;
             m[k] = mc;
             v[k] = vc;
-            prm[k] -= step * mc / (sqrtf(vc) / bc2_sqrt + eps);
         }
     }
 }
 
 }  // namespace dg
+
+dg::AdamHp dg_adam_hp(const float* lr, float beta1, float beta2, float eps, int64_t step)
+{
+    dg::AdamHp h;
+    for (int i = 0; i < DG_NPARAM; ++i) h.lr[i] = lr[i];
+    h.b1 = beta1;
+    h.b2 = beta2;
+    h.bc1 = (float)(1.0 - pow((double)beta1, (double)step));
+    h.bc2_sqrt = (float)sqrt(1.0 - pow((double)beta2, (double)step));
+    h.eps = eps;
+    return h;
+}
 
 extern "C" size_t dg_loss_workspace_size(int64_t n)
 {
@@ -160,14 +162,10 @@ extern "C" dg_status dg_adam_step(float* params, const float* grads, float* m, f
     if (P < 0 || stride < P || step < 1) { dg_set_error("bad P/stride/step"); return DG_ERR_ARG; }
     if (P == 0) return DG_OK;
     if (!params || !grads || !m || !v || !lr) { dg_set_error("null buffer"); return DG_ERR_ARG; }
-    dg::AdamRow r;
-    for (int i = 0; i < DG_NPARAM; ++i) r.lr[i] = lr[i];
-    const double bc1 = 1.0 - pow((double)beta1, (double)step);
-    const double bc2 = 1.0 - pow((double)beta2, (double)step);
+    const dg::AdamHp hp = dg_adam_hp(lr, beta1, beta2, eps, step);
     const long long per = 256 * 4;
     dim3 grid((unsigned)((P + per - 1) / per), DG_NPARAM);
-    dg::k_adam<<<grid, 256, 0, (cudaStream_t)stream>>>(params, grads, m, v, stride, P, r, beta1, beta2,
-                                                        (float)bc1, (float)sqrt(bc2), eps);
+    dg::k_adam<<<grid, 256, 0, (cudaStream_t)stream>>>(params, grads, m, v, stride, P, hp);
     dg_note_launch();
     return dg_check_launch("adam");
 }

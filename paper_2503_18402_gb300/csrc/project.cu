@@ -245,14 +245,30 @@ k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs
     }
 }
 
-template <int NB>
+// Adjoint of the projection, summed over the views.  Each parameter-row
+// gradient goes to `grads` (when given) and, with ADAM, straight into the Adam
+// update of that row (params, m, v), so the fused form never stores or reloads
+// the gradient and reads the parameters once.  Each thread owns one Gaussian
+// (one column of every row), so the in-place update races with nothing.
+template <int NB, bool ADAM>
 __global__ void __launch_bounds__(128)
-k_project_bwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs, float near_plane, float eps2d,
+k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs, float near_plane, float eps2d,
               const int* __restrict__ radius, const uint8_t* __restrict__ clampm, const float4* __restrict__ grad2d,
-              float* __restrict__ grads)
+              float* __restrict__ grads, float* __restrict__ am, float* __restrict__ av, AdamHp hp)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
+    auto put = [&](int row, float gval) {
+        const long long o = (long long)row * stride + i;
+        if (grads) grads[o] = gval;
+        if (ADAM) {
+            float p = prm[o], mm = am[o], vv = av[o];
+            adam_update(p, mm, vv, gval, hp.lr[row], hp);
+            prm[o] = p;
+            am[o] = mm;
+            av[o] = vv;
+        }
+    };
     G3 g;
     gauss3d(prm, stride, i, g);
     float dp[3] = {0.f, 0.f, 0.f};
@@ -359,20 +375,20 @@ k_project_bwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs
         for (int c = 0; c < 3; ++c) dp[c] += rc[c] * dt[0] + rc[3 + c] * dt[1] + rc[6 + c] * dt[2];
     }
     if (!any) {
-        for (int rr = 0; rr < DG_NPARAM; ++rr) grads[rr * stride + i] = 0.f;
+        for (int rr = 0; rr < DG_NPARAM; ++rr) put(rr, 0.f);
         return;
     }
-    grads[i] = dp[0];
-    grads[stride + i] = dp[1];
-    grads[2 * stride + i] = dp[2];
+    put(0, dp[0]);
+    put(1, dp[1]);
+    put(2, dp[2]);
     {
         const float o = 1.f / (1.f + expf(-prm[10 * stride + i]));
-        grads[10 * stride + i] = dop * o * (1.f - o);
+        put(10, dop * o * (1.f - o));
     }
 #pragma unroll
     for (int k = 0; k < 16; ++k)
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) grads[(11 + 3 * k + ch) * stride + i] = k < NB ? dsh[k][ch] : 0.f;
+        for (int ch = 0; ch < 3; ++ch) put(11 + 3 * k + ch, k < NB ? dsh[k][ch] : 0.f);
     // Sigma = M M^T:  dM = 2 dSigma M;  M = Rq diag(s)
     const float ds[9] = {dsg[0], dsg[1], dsg[2], dsg[1], dsg[3], dsg[4], dsg[2], dsg[4], dsg[5]};
     float dR[9];
@@ -385,7 +401,7 @@ k_project_bwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs
             dsc += dm * g.rq[3 * rr + c];
             dR[3 * rr + c] = dm * g.s[c];
         }
-        grads[(3 + c) * stride + i] = dsc * g.s[c];
+        put(3 + c, dsc * g.s[c]);
     }
     const float w = g.qn[0], x = g.qn[1], y = g.qn[2], z = g.qn[3];
     float dq[4];
@@ -395,7 +411,7 @@ k_project_bwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs
     dq[3] = 2.f * (w * (dR[3] - dR[1]) + x * (dR[2] + dR[6]) + y * (dR[5] + dR[7]) - 2.f * z * (dR[0] + dR[4]));
     const float qd = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) grads[(6 + c) * stride + i] = (dq[c] - g.qn[c] * qd) * g.qinv;
+    for (int c = 0; c < 4; ++c) put(6 + c, (dq[c] - g.qn[c] * qd) * g.qinv);
 }
 
 }  // namespace dg
@@ -462,9 +478,11 @@ extern "C" dg_status dg_project(const float* params, int64_t stride, int64_t P, 
     return dg_check_launch("project_fwd");
 }
 
-extern "C" dg_status dg_project_bwd(const float* params, int64_t stride, int64_t P, const dg_camera* cams,
-                                    int32_t n_views, const dg_raster_opts* opts, const int32_t* radius,
-                                    const uint8_t* clamp, const float* grad2d, float* grads, dg_stream stream)
+template <bool ADAM>
+static dg_status project_bwd(float* params, int64_t stride, int64_t P, const dg_camera* cams, int32_t n_views,
+                             const dg_raster_opts* opts, const int32_t* radius, const uint8_t* clamp,
+                             const float* grad2d, float* grads, float* m, float* v, const dg::AdamHp& hp,
+                             dg_stream stream)
 {
     if (!dg_check_cameras(cams, n_views) || !check_opts(opts)) return DG_ERR_ARG;
     if (P < 0 || P > INT32_MAX || stride < P || (long long)P * n_views > (long long)UINT32_MAX) {
@@ -472,18 +490,43 @@ extern "C" dg_status dg_project_bwd(const float* params, int64_t stride, int64_t
         return DG_ERR_ARG;
     }
     if (P == 0) return DG_OK;
-    if (!params || !radius || !clamp || !grad2d || !grads) { dg_set_error("null buffer"); return DG_ERR_ARG; }
+    if (!params || !radius || !clamp || !grad2d || (!ADAM && !grads) || (ADAM && (!m || !v))) {
+        dg_set_error("null buffer");
+        return DG_ERR_ARG;
+    }
     if (((uintptr_t)grad2d) & 15u) { dg_set_error("grad2d must be 16-byte aligned"); return DG_ERR_ARG; }
     const dg::ViewSet vs = make_views(cams, n_views, opts->tile);
     const int threads = 128;
     const int blocks = (int)((P + threads - 1) / threads);
     cudaStream_t s = (cudaStream_t)stream;
+    const long long st = (long long)stride;
+    const float4* g2 = (const float4*)grad2d;
     switch (opts->sh_degree) {
-    case 0: dg::k_project_bwd<1><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, opts->near_plane, opts->eps2d, radius, clamp, (const float4*)grad2d, grads); break;
-    case 1: dg::k_project_bwd<4><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, opts->near_plane, opts->eps2d, radius, clamp, (const float4*)grad2d, grads); break;
-    case 2: dg::k_project_bwd<9><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, opts->near_plane, opts->eps2d, radius, clamp, (const float4*)grad2d, grads); break;
-    default: dg::k_project_bwd<16><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, opts->near_plane, opts->eps2d, radius, clamp, (const float4*)grad2d, grads); break;
+    case 0: dg::k_project_bwd<1, ADAM><<<blocks, threads, 0, s>>>(params, st, (int)P, vs, opts->near_plane, opts->eps2d, radius, clamp, g2, grads, m, v, hp); break;
+    case 1: dg::k_project_bwd<4, ADAM><<<blocks, threads, 0, s>>>(params, st, (int)P, vs, opts->near_plane, opts->eps2d, radius, clamp, g2, grads, m, v, hp); break;
+    case 2: dg::k_project_bwd<9, ADAM><<<blocks, threads, 0, s>>>(params, st, (int)P, vs, opts->near_plane, opts->eps2d, radius, clamp, g2, grads, m, v, hp); break;
+    default: dg::k_project_bwd<16, ADAM><<<blocks, threads, 0, s>>>(params, st, (int)P, vs, opts->near_plane, opts->eps2d, radius, clamp, g2, grads, m, v, hp); break;
     }
     dg_note_launch();
-    return dg_check_launch("project_bwd");
+    return dg_check_launch(ADAM ? "project_bwd_adam" : "project_bwd");
+}
+
+extern "C" dg_status dg_project_bwd(const float* params, int64_t stride, int64_t P, const dg_camera* cams,
+                                    int32_t n_views, const dg_raster_opts* opts, const int32_t* radius,
+                                    const uint8_t* clamp, const float* grad2d, float* grads, dg_stream stream)
+{
+    // the non-Adam instantiation never writes params
+    return project_bwd<false>(const_cast<float*>(params), stride, P, cams, n_views, opts, radius, clamp, grad2d,
+                              grads, nullptr, nullptr, dg::AdamHp{}, stream);
+}
+
+extern "C" dg_status dg_project_bwd_adam(float* params, int64_t stride, int64_t P, const dg_camera* cams,
+                                         int32_t n_views, const dg_raster_opts* opts, const int32_t* radius,
+                                         const uint8_t* clamp, const float* grad2d, float* grads, float* m, float* v,
+                                         const float* lr, float beta1, float beta2, float eps, int64_t step,
+                                         dg_stream stream)
+{
+    if (step < 1 || !lr) { dg_set_error("step must be >= 1 and lr given"); return DG_ERR_ARG; }
+    return project_bwd<true>(params, stride, P, cams, n_views, opts, radius, clamp, grad2d, grads, m, v,
+                             dg_adam_hp(lr, beta1, beta2, eps, step), stream);
 }

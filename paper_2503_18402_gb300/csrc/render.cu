@@ -1,24 +1,47 @@
 // render.cu -- Eq. 1 compositing per tile (forward) and its adjoint (backward).
 //
-// Persistent launch over all views: one CTA per resident slot, each taking
-// (view, tile) work items from an atomic counter until none are left, so
-// tiles of very different cost (list lengths differ by orders of magnitude)
-// balance across the SMs and all views of a batch share one launch.  A work
-// item is a B x B tile; each thread owns PPT pixels of one column of the
-// tile (rows ly, ly + B/PPT, ...).  The tile's sorted list is streamed through
-// shared memory in batches of B*B/PPT records (one coalesced 48-byte gather per
-// thread per batch); every staged record is then evaluated for the thread's
-// PPT pixels, so shared-memory loads and loop control are shared by PPT
-// evaluations.
-//   Forward: front to back; a CTA stops once every pixel has terminated
+// Persistent launches over all views: one CTA per resident slot, each taking
+// work items from an atomic counter until none are left, so items of very
+// different cost balance across the SMs and all views of a batch share one
+// launch.  Each thread owns PPT pixels of one column of a B x B tile (rows
+// ly, ly + B/PPT, ...).  A work item's list entries are streamed through
+// shared memory in batches of B*B/PPT records (one coalesced 48-byte gather
+// per thread per batch); every staged record is then evaluated for the
+// thread's PPT pixels.
+//
+// Work items.  Without splitting, an item is a whole tile.  A tile's list is
+// walked in order, so a tile with a long list is a serial chain that no other
+// SM can help with; at low resolution (few tiles, thousands of entries each)
+// those chains set the time of the launch.  With splitting, a tile whose list
+// is longer than L entries becomes ceil(n/L) chunks of L entries, each its own
+// work item.  Eq. 1 composes over chunks: the transmittance in front of
+// chunk c is the product of the (1 - alpha) factors of chunks 0..c-1, and the
+// colour is the sum of the chunks' contributions.  Three passes keep the
+// result that of the sequential rule, early stop included:
+//   1. product pass: each chunk but the last computes, per pixel, the product
+//      of its (1 - alpha) factors starting from 1, stopping as soon as the
+//      product drops below the stop threshold (from then on the pixel has
+//      stopped whatever the transmittance in front of the chunk);
+//   2. compositing pass: each chunk starts from T_in = product of the earlier
+//      chunks' products and applies Eq. 1 with the stop rule exactly; a pixel
+//      whose T_in is already below the threshold stopped in an earlier chunk;
+//   3. combine: per pixel, the colour sum over chunks, T_final from the chunk
+//      where compositing stopped (else the last chunk), last = the largest
+//      last of any chunk; and, for the backward, the colour behind each chunk.
+// The backward takes the same items: a chunk starts from its own end
+// transmittance and the colour behind it instead of T_final and T_final * bg.
+// By default lists are split only when the batch has fewer than two tiles per
+// resident CTA, with L = max(64, M / resident CTAs); L is raised where needed
+// to keep the chunk count within the workspace.
+//
+//   Forward: front to back; an item stops once every pixel has terminated
 //   (__syncthreads_count).
 //   Backward: back to front from each pixel's last contributor; the
-//   transmittance in front of entry j is recovered as T_j = T_{j+1} / (1 - a_j)
-//   from the stored final T.  A thread first sums its PPT pixels' partial
-//   gradients, the warp then sums the nine values by recursive halving (12
-//   shuffles) and nine lanes add the totals with one atomic instruction; warps
-//   with no contributing pixel skip the reduction.  Larger PPT divides the reduction
-//   and atomic cost per evaluated (pixel, Gaussian) entry.
+//   transmittance in front of entry j is recovered as T_j = T_{j+1} / (1 - a_j).
+//   A thread first sums its PPT pixels' partial gradients, the warp then sums
+//   the nine values by recursive halving (12 shuffles) and nine lanes add the
+//   totals with one atomic instruction; warps with no contributing pixel skip
+//   the reduction.
 // Tile-level skip: while a batch is staged, each entry is tested once against
 // the whole tile: the minimum of its quadratic form over the rectangle of the
 // tile's pixel centres (closed form on the four edges when the mean lies
@@ -26,7 +49,10 @@
 // absorbs float32 rounding of the per-pixel evaluation), every pixel would
 // skip the entry, so it is dropped from the batch (stable compaction; the
 // original list position is kept for `last`).  Results are unchanged.
+#include <climits>
+
 #include "common.cuh"
+#include "radix.cuh"
 
 namespace dg {
 
@@ -102,24 +128,128 @@ __device__ inline int compact_index(bool keep, int* s_w, int* total)
 // pixels start in the global tile range table and the concatenated images.
 struct RViews {
     int n;
-    int total;                      // work items = tiles of all views
+    int total;                      // tiles of all views
     int W[DG_MAX_VIEWS], H[DG_MAX_VIEWS], TX[DG_MAX_VIEWS];
     int toff[DG_MAX_VIEWS + 1];
     long long poff[DG_MAX_VIEWS];   // first pixel of each view
     float bg0, bg1, bg2;
 };
 
-struct Item { int tile, v, tx, ty, W, H; long long poff; };
+// Head of the render workspace.  The forward writes the split plan here and
+// in the arrays after it; the backward of the same batch reads it.
+struct RHdr {
+    int cnt_prod, cnt_fwd, cnt_bwd, cnt_pad;  // work counters of the three persistent launches
+    int planned;                              // 1: items/sitems hold a split plan
+    int L;                                    // chunk length of that plan
+    int n_items, n_slots;                     // items (all chunks), chunks of split tiles
+    long long M;                              // entries in the range table
+    long long totals;                         // scan total: items (low 32 bits), split chunks (high 32)
+};
+static_assert(sizeof(RHdr) <= 256, "render header");
 
-// Next work item of this CTA (item.tile < 0: none left).  Ends with a barrier.
-__device__ inline Item next_item(int* counter, const RViews& rv, int* s_item)
+// Per-pixel state of split chunks: planes [cap][B*B], chunk slot s = slot0 + c.
+struct Slots {
+    float* prod;   // product of the chunk's (1 - alpha), pass 1
+    float* tout;   // transmittance at the chunk's end (or where compositing stopped)
+    float* c0;     // colour added by the chunk; after the combine, the colour behind it
+    float* c1;
+    float* c2;
+    int* last;     // 1-based list position of the chunk's last blend | kStopFlag if it stopped there
+    int* nbl;      // entries blended in the chunk
+    int* stop;     // list position where compositing stopped (-1 if not in this chunk)
+};
+constexpr int kStopFlag = 1 << 30;
+
+struct SplitCfg {
+    int Lreq;  // > 0: requested chunk length; 0: automatic
+    int R;     // resident CTAs of the compositing launch
+    int cap;   // chunk slots in the workspace
+};
+
+// Chunk length for M entries: requested or max(64, M/R), raised to 2M/cap so
+// that the chunks of split tiles (each tile has n > L, so ceil(n/L) < 2n/L)
+// never exceed the slots.
+__host__ __device__ inline int split_len(long long M, SplitCfg s)
 {
-    if (threadIdx.x == 0) *s_item = atomicAdd(counter, 1);
+    long long L = s.Lreq > 0 ? s.Lreq : (M + s.R - 1) / s.R;
+    if (s.Lreq <= 0 && L < 64) L = 64;
+    const long long Lcap = (2 * M + s.cap - 1) / s.cap;
+    if (L < Lcap) L = Lcap;
+    if (L < 1) L = 1;
+    if (L > (INT_MAX >> 2)) L = INT_MAX >> 2;
+    return (int)L;
+}
+
+struct LoadLen {
+    const uint2* ranges;
+    __device__ uint64_t operator()(long long t) const { const uint2 r = ranges[t]; return (uint64_t)(r.y - r.x); }
+};
+// Items (low 32 bits) and split chunks (high 32 bits) of tile t.
+struct LoadChunks {
+    const uint2* ranges;
+    const RHdr* hdr;
+    SplitCfg cfg;
+    __device__ uint64_t operator()(long long t) const
+    {
+        const long long L = split_len(hdr->M, cfg);
+        const uint2 r = ranges[t];
+        const long long n = (long long)(r.y - r.x);
+        if (n <= L) return 1;
+        const uint64_t k = (uint64_t)((n + L - 1) / L);
+        return (k << 32) | k;
+    }
+};
+
+__global__ void k_plan_items(const uint2* __restrict__ ranges, int n_tiles, RHdr* hdr, SplitCfg cfg,
+                             const uint64_t* __restrict__ toff, int4* __restrict__ items, int4* __restrict__ sitems)
+{
+    const long long M = hdr->M;
+    const int L = split_len(M, cfg);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned long long tot = (unsigned long long)hdr->totals;
+        hdr->L = L;
+        hdr->n_items = (int)(tot & 0xffffffffull);
+        hdr->n_slots = (int)(tot >> 32);
+        hdr->planned = 1;
+    }
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
+        const uint2 r = ranges[t];
+        const long long n = (long long)(r.y - r.x);  // as counted by LoadChunks
+        const uint64_t off = toff[t];
+        const int io = (int)(off & 0xffffffffull), so = (int)(off >> 32);
+        if (n <= L) {
+            items[io] = make_int4(t, 0, 1, -1);
+            continue;
+        }
+        const int k = (int)((n + L - 1) / L);
+        for (int c = 0; c < k; ++c) {
+            const int4 w = make_int4(t, c, k, so);
+            items[io + c] = w;
+            sitems[so + c] = w;
+        }
+    }
+}
+
+// A work item: tile (global over views), chunk c of nch, first chunk slot
+// (-1: the tile is not split), and the tile's place in its view.
+struct Item { int tile, c, nch, slot0, v, tx, ty, W, H; long long poff; };
+
+// Next work item of this CTA from `list` (or tile `index` when list is null);
+// item.tile < 0: none left.  Ends with a barrier.
+__device__ inline Item next_item(int* counter, int count, const int4* list, const RViews& rv, int4* s_item)
+{
+    if (threadIdx.x == 0) {
+        const int i = atomicAdd(counter, 1);
+        int4 w = make_int4(-1, 0, 1, -1);
+        if (i < count) w = list ? list[i] : make_int4(i, 0, 1, -1);
+        *s_item = w;
+    }
+    __syncthreads();
+    const int4 w = *s_item;
     __syncthreads();
     Item it;
-    it.tile = *s_item;
-    __syncthreads();
-    if (it.tile >= rv.total) { it.tile = -1; return it; }
+    it.tile = w.x; it.c = w.y; it.nch = w.z; it.slot0 = w.w;
+    if (it.tile < 0) return it;
     int v = 0;
     while (v + 1 < rv.n && it.tile >= rv.toff[v + 1]) ++v;
     const int t = it.tile - rv.toff[v];
@@ -132,30 +262,48 @@ __device__ inline Item next_item(int* counter, const RViews& rv, int* s_item)
     return it;
 }
 
-template <int B, int PPT>
+// Compositing of one work item.  PROD: pass 1 of a split tile (product of
+// the chunk's (1 - alpha) factors from 1, no colour).  Otherwise Eq. 1 over
+// the item's entries from T_in, writing the final pixels (whole tile) or the
+// chunk's slot (split tile).
+template <int B, int PPT, bool PROD>
 __global__ void __launch_bounds__(B * B / PPT)
 k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
-             const uint2* __restrict__ ranges, RViews rv, int* __restrict__ counter,
+             const uint2* __restrict__ ranges, RViews rv, RHdr* hdr, const int4* __restrict__ items,
+             const int4* __restrict__ sitems, Slots sl,
              float* __restrict__ img, float* __restrict__ Tout, int* __restrict__ lastout,
              int* __restrict__ exout, int* __restrict__ blout)
 {
     constexpr int NT = B * B / PPT;
+    constexpr int NPIX = B * B;
     constexpr int RSTEP = B / PPT;  // row step between a thread's pixels
     __shared__ float4 s_a[NT];  // u, v, A, B
     __shared__ float4 s_b[NT];  // C, o, r, g
     __shared__ float s_c[NT];   // b
     __shared__ int s_pos[NT];   // list position
     __shared__ int s_w[NT / 32];
-    __shared__ int s_item;
+    __shared__ int4 s_item;
+    const bool planned = hdr->planned != 0 && items != nullptr;
+    const int L = planned ? hdr->L : INT_MAX;
+    const int count = PROD ? hdr->n_slots : (planned ? hdr->n_items : rv.total);
+    const int4* list = PROD ? sitems : (planned ? items : nullptr);
+    int* counter = PROD ? &hdr->cnt_prod : &hdr->cnt_fwd;
     for (;;) {
-    const Item it = next_item(counter, rv, &s_item);
+    const Item it = next_item(counter, count, list, rv, &s_item);
     if (it.tile < 0) break;
+    if (PROD && it.c == it.nch - 1) continue;  // the last chunk's product is never needed
     const int tile = it.tile, tx = it.tx, ty = it.ty, W = it.W, H = it.H;
-    const int x = tx * B + (int)(threadIdx.x % B);
-    const int y0 = ty * B + (int)(threadIdx.x / B);
+    const int lx = (int)(threadIdx.x % B), ly0 = (int)(threadIdx.x / B);
+    const int x = tx * B + lx;
+    const int y0 = ty * B + ly0;
     const float pxc = (float)x + 0.5f;
     const float tpx0 = (float)(tx * B) + 0.5f, tpx1 = tpx0 + (float)(B - 1);
     const float tpy0 = (float)(ty * B) + 0.5f, tpy1 = tpy0 + (float)(B - 1);
+    const uint2 rg = ranges[tile];
+    const int n = (int)(rg.y - rg.x);
+    const bool split = it.slot0 >= 0;
+    const int lo = split ? it.c * L : 0;
+    const int hi = split ? (int)min((long long)n, (long long)lo + L) : n;
     float pyc[PPT], T[PPT], c0[PPT], c1[PPT], c2[PPT];
     int last[PPT], stop[PPT], nbl[PPT];
     bool done[PPT];
@@ -166,19 +314,23 @@ k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
         T[k] = 1.f; c0[k] = c1[k] = c2[k] = 0.f;
         last[k] = 0; stop[k] = -1; nbl[k] = 0;
         done[k] = !(x < W && y < H);
+        if (!PROD && split && it.c > 0) {
+            // transmittance in front of the chunk: product of the earlier chunks' products
+            const int p = (ly0 + k * RSTEP) * B + lx;
+            for (int c = 0; c < it.c; ++c) T[k] *= sl.prod[(size_t)(it.slot0 + c) * NPIX + p];
+            if (T[k] < kTMin) done[k] = true;  // stopped in an earlier chunk
+        }
     }
     bool alldone = true;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) alldone = alldone && done[k];
-    const uint2 rg = ranges[tile];
-    const int n = (int)(rg.y - rg.x);
-    for (int base = 0; base < n; base += NT) {
+    for (int base = lo; base < hi; base += NT) {
         if (__syncthreads_count(alldone) == NT) break;
         const int j = base + (int)threadIdx.x;
         bool keep = false;
         float4 ga, gb;
         float gc = 0.f;
-        if (j < n) {
+        if (j < hi) {
             const uint32_t g = gid[rg.x + j];
             ga = feat[3 * (size_t)g];
             gb = feat[3 * (size_t)g + 1];
@@ -214,20 +366,40 @@ k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
                         if (Tn < kTMin) {
                             done[k] = true;
                             stop[k] = pos;
+                            if (PROD) T[k] = Tn;  // below the threshold: every later chunk is stopped
                         } else {
-                            const float w = alpha * T[k];
-                            c0[k] += w * b.z;
-                            c1[k] += w * b.w;
-                            c2[k] += w * cb;
+                            if (!PROD) {
+                                const float w = alpha * T[k];
+                                c0[k] += w * b.z;
+                                c1[k] += w * b.w;
+                                c2[k] += w * cb;
+                                last[k] = pos + 1;
+                                ++nbl[k];
+                            }
                             T[k] = Tn;
-                            last[k] = pos + 1;
-                            ++nbl[k];
                         }
                     }
                 }
                 alldone = alldone && done[k];
             }
         }
+    }
+    if (split) {
+        const size_t s0 = (size_t)(it.slot0 + it.c) * NPIX;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            const size_t s = s0 + (size_t)((ly0 + k * RSTEP) * B + lx);
+            if (PROD) {
+                sl.prod[s] = T[k];
+            } else {
+                sl.tout[s] = T[k];
+                sl.c0[s] = c0[k]; sl.c1[s] = c1[k]; sl.c2[s] = c2[k];
+                sl.last[s] = last[k] | (stop[k] >= 0 ? kStopFlag : 0);
+                sl.nbl[s] = nbl[k];
+                sl.stop[s] = stop[k];
+            }
+        }
+        continue;
     }
     const size_t HW = (size_t)W * H;
     float* im = img + 3 * it.poff;
@@ -247,6 +419,65 @@ k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
         }
     }
     }  // work items
+}
+
+// Pass 3 of split tiles: one CTA per split tile, one thread per pixel.
+template <int B>
+__global__ void __launch_bounds__(B * B)
+k_render_combine(const uint2* __restrict__ ranges, RViews rv, const RHdr* hdr, const int4* __restrict__ sitems,
+                 Slots sl, float* __restrict__ img, float* __restrict__ Tout, int* __restrict__ lastout,
+                 int* __restrict__ exout, int* __restrict__ blout)
+{
+    constexpr int NPIX = B * B;
+    if (!hdr->planned) return;
+    const int count = hdr->n_slots;
+    for (int i = blockIdx.x; i < count; i += gridDim.x) {
+        const int4 w = sitems[i];
+        if (w.y != 0) continue;
+        int v = 0;
+        while (v + 1 < rv.n && w.x >= rv.toff[v + 1]) ++v;
+        const int t = w.x - rv.toff[v];
+        const int W = rv.W[v], H = rv.H[v];
+        const int lx = (int)(threadIdx.x % B), ly = (int)(threadIdx.x / B);
+        const int x = (t % rv.TX[v]) * B + lx, y = (t / rv.TX[v]) * B + ly;
+        if (!(x < W && y < H)) continue;
+        const uint2 rg = ranges[w.x];
+        const int n = (int)(rg.y - rg.x);
+        const int nch = w.z;
+        const size_t p = (size_t)threadIdx.x;
+        float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tf = -1.f;
+        int lastv = 0, nb = 0, ex = n;
+        for (int c = 0; c < nch; ++c) {
+            const size_t s = (size_t)(w.w + c) * NPIX + p;
+            const int lt = sl.last[s];
+            C0 += sl.c0[s]; C1 += sl.c1[s]; C2 += sl.c2[s];
+            lastv = max(lastv, lt & (kStopFlag - 1));
+            nb += sl.nbl[s];
+            if ((lt & kStopFlag) && Tf < 0.f) {
+                Tf = sl.tout[s];
+                ex = sl.stop[s] + 1;
+            }
+        }
+        if (Tf < 0.f) Tf = sl.tout[(size_t)(w.w + nch - 1) * NPIX + p];
+        // colour behind each chunk (the backward's starting S), back to front
+        float S0 = Tf * rv.bg0, S1 = Tf * rv.bg1, S2 = Tf * rv.bg2;
+        for (int c = nch - 1; c >= 0; --c) {
+            const size_t s = (size_t)(w.w + c) * NPIX + p;
+            const float a0 = sl.c0[s], a1 = sl.c1[s], a2 = sl.c2[s];
+            sl.c0[s] = S0; sl.c1[s] = S1; sl.c2[s] = S2;
+            S0 += a0; S1 += a1; S2 += a2;
+        }
+        const size_t HW = (size_t)W * H;
+        const size_t pix = (size_t)y * W + x;
+        float* im = img + 3 * rv.poff[v];
+        im[pix] = C0 + Tf * rv.bg0;
+        im[HW + pix] = C1 + Tf * rv.bg1;
+        im[2 * HW + pix] = C2 + Tf * rv.bg2;
+        Tout[rv.poff[v] + pix] = Tf;
+        lastout[rv.poff[v] + pix] = lastv;
+        if (exout) exout[rv.poff[v] + pix] = ex;
+        if (blout) blout[rv.poff[v] + pix] = nb;
+    }
 }
 
 // Sum of 9 per-lane values over the warp by recursive halving: at each step a
@@ -294,11 +525,12 @@ __device__ inline float warp_sum9(const float v[9], int lane, int* idx)
 template <int B, int PPT>
 __global__ void __launch_bounds__(B * B / PPT)
 k_render_bwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
-             const uint2* __restrict__ ranges, RViews rv, int* __restrict__ counter,
+             const uint2* __restrict__ ranges, RViews rv, RHdr* hdr, const int4* __restrict__ items, Slots sl,
              const float* __restrict__ Tfin, const int* __restrict__ lastin,
              const float* __restrict__ dLdimg, float4* __restrict__ grad2d)
 {
     constexpr int NT = B * B / PPT;
+    constexpr int NPIX = B * B;
     constexpr int RSTEP = B / PPT;
     __shared__ float4 s_a[NT];
     __shared__ float4 s_b[NT];
@@ -307,18 +539,28 @@ k_render_bwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
     __shared__ int s_pos[NT];
     __shared__ int s_w[NT / 32];
     __shared__ int s_n;
-    __shared__ int s_item;
+    __shared__ int4 s_item;
     const float bg0 = rv.bg0, bg1 = rv.bg1, bg2 = rv.bg2;
+    // (a whole-tile walk is exact whatever the forward did; items is null when
+    // the workspace was laid out without splitting)
+    const bool planned = hdr->planned != 0 && items != nullptr;
+    const int L = planned ? hdr->L : INT_MAX;
+    const int count = planned ? hdr->n_items : rv.total;
     for (;;) {
-    const Item it = next_item(counter, rv, &s_item);
+    const Item it = next_item(&hdr->cnt_bwd, count, planned ? items : nullptr, rv, &s_item);
     if (it.tile < 0) break;
     const int tile = it.tile, tx = it.tx, ty = it.ty, W = it.W, H = it.H;
-    const int x = tx * B + (int)(threadIdx.x % B);
-    const int y0 = ty * B + (int)(threadIdx.x / B);
+    const int lx = (int)(threadIdx.x % B), ly0 = (int)(threadIdx.x / B);
+    const int x = tx * B + lx;
+    const int y0 = ty * B + ly0;
     const float pxc = (float)x + 0.5f;
     const float tpx0 = (float)(tx * B) + 0.5f, tpx1 = tpx0 + (float)(B - 1);
     const float tpy0 = (float)(ty * B) + 0.5f, tpy1 = tpy0 + (float)(B - 1);
     const uint2 rg = ranges[tile];
+    const int nlist = (int)(rg.y - rg.x);
+    const bool split = it.slot0 >= 0;
+    const int lo = split ? it.c * L : 0;
+    const int hi = split ? (int)min((long long)nlist, (long long)lo + L) : nlist;
     const size_t HW = (size_t)W * H;
     float pyc[PPT], T[PPT], g0[PPT], g1[PPT], g2[PPT], S0[PPT], S1[PPT], S2[PPT];
     int lastp[PPT];
@@ -328,32 +570,40 @@ k_render_bwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
         const int y = y0 + k * RSTEP;
         pyc[k] = (float)y + 0.5f;
         T[k] = 1.f; g0[k] = g1[k] = g2[k] = 0.f; lastp[k] = 0;
+        S0[k] = S1[k] = S2[k] = 0.f;
         if (x < W && y < H) {
             const size_t pix = (size_t)y * W + x;
             const float* dl = dLdimg + 3 * it.poff;
-            T[k] = Tfin[it.poff + pix];
             lastp[k] = lastin[it.poff + pix];
             g0[k] = dl[pix];
             g1[k] = dl[HW + pix];
             g2[k] = dl[2 * HW + pix];
+            if (split) {
+                // the chunk's end transmittance and the colour behind the chunk
+                const size_t s = (size_t)(it.slot0 + it.c) * NPIX + (size_t)((ly0 + k * RSTEP) * B + lx);
+                T[k] = sl.tout[s];
+                S0[k] = sl.c0[s]; S1[k] = sl.c1[s]; S2[k] = sl.c2[s];
+            } else {
+                T[k] = Tfin[it.poff + pix];
+                S0[k] = T[k] * bg0; S1[k] = T[k] * bg1; S2[k] = T[k] * bg2;  // colour behind the last entry
+            }
         }
-        S0[k] = T[k] * bg0; S1[k] = T[k] * bg1; S2[k] = T[k] * bg2;  // colour behind the current entry
         mylast = max(mylast, lastp[k]);
     }
     if (threadIdx.x == 0) s_n = 0;
     __syncthreads();
     if (mylast > 0) atomicMax(&s_n, mylast);
     __syncthreads();
-    // never walk past the tile's own list, whatever `last` holds
-    const int n = min(s_n, (int)(rg.y - rg.x));
+    // never walk past the item's own entries, whatever `last` holds
+    const int top = min(s_n, hi);
     const int lane = threadIdx.x & 31;
-    for (int base = ((n - 1) / NT) * NT; n > 0 && base >= 0; base -= NT) {
+    for (int base = top > lo ? lo + ((top - lo - 1) / NT) * NT : lo - 1; base >= lo; base -= NT) {
         const int j = base + (int)threadIdx.x;
         bool keep = false;
         float4 ga, gb;
         float gc = 0.f;
         uint32_t g = 0;
-        if (j < n) {
+        if (j < top) {
             g = gid[rg.x + j];
             ga = feat[3 * (size_t)g];
             gb = feat[3 * (size_t)g + 1];
@@ -446,37 +696,110 @@ static dg::RViews make_rviews(const dg_camera* cams, int n, int B, const dg_rast
     return rv;
 }
 
-// CTAs of a persistent launch: every resident slot of the device, at most one per item.
+// Resident CTAs of a kernel on this device.
 template <typename Kern>
-static int persistent_grid(Kern kern, int threads, int items)
+static int resident_ctas(Kern kern, int threads)
 {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
-    long long g = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-    if (g > items) g = items;
-    return (int)(g > 0 ? g : 1);
+    const long long g = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    return (int)(g < (1 << 20) ? g : (1 << 20));
+}
+
+// Layout of the render workspace for n_tiles tiles of edge B.
+struct RenderWs {
+    dg::RHdr* hdr;
+    int4* items;
+    int4* sitems;
+    uint64_t* toff;
+    uint64_t* bsum;
+    dg::Slots sl;
+    int cap;
+    size_t bytes;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Chunk slots: 2^20 pixels' worth (32 MiB of per-pixel chunk state).
+static int slot_cap(int B) { return (1 << 20) / (B * B); }
+
+static RenderWs render_ws(void* base, long long n_tiles, int B, bool split)
+{
+    RenderWs w{};
+    char* p = (char*)base;
+    size_t off = 256;
+    w.hdr = (dg::RHdr*)p;
+    if (!split) { w.bytes = off; return w; }
+    const int cap = slot_cap(B);
+    const long long nb = (n_tiles + dg::SCAN_TILE - 1) / dg::SCAN_TILE;
+    const size_t npix = (size_t)cap * B * B;
+    w.cap = cap;
+    w.items = (int4*)(p + off);  off = align256(off + sizeof(int4) * (size_t)(n_tiles + cap));
+    w.sitems = (int4*)(p + off); off = align256(off + sizeof(int4) * (size_t)cap);
+    w.toff = (uint64_t*)(p + off); off = align256(off + sizeof(uint64_t) * (size_t)(n_tiles > 0 ? n_tiles : 1));
+    w.bsum = (uint64_t*)(p + off); off = align256(off + sizeof(uint64_t) * (size_t)(nb > 0 ? nb : 1));
+    float** fp[5] = {&w.sl.prod, &w.sl.tout, &w.sl.c0, &w.sl.c1, &w.sl.c2};
+    for (int i = 0; i < 5; ++i) { *fp[i] = (float*)(p + off); off = align256(off + sizeof(float) * npix); }
+    int** ip[3] = {&w.sl.last, &w.sl.nbl, &w.sl.stop};
+    for (int i = 0; i < 3; ++i) { *ip[i] = (int*)(p + off); off = align256(off + sizeof(int) * npix); }
+    w.bytes = off;
+    return w;
 }
 
 template <int B, int PPT>
-static void launch_fwd(const float* feat, const uint32_t* gid, const uint32_t* ranges, const dg::RViews& rv,
-                       int* counter, float* img, float* T, int* last, int* ex, int* bl, cudaStream_t s)
+static dg_status launch_fwd(const float* feat, const uint32_t* gid, const uint32_t* ranges, const dg::RViews& rv,
+                            const RenderWs& w, int split_req, float* img, float* T, int* last, int* ex, int* bl,
+                            cudaStream_t s)
 {
-    auto kern = dg::k_render_fwd<B, PPT>;
-    const int grid = persistent_grid(kern, B * B / PPT, rv.total);
-    kern<<<grid, B * B / PPT, 0, s>>>((const float4*)feat, gid, (const uint2*)ranges, rv, counter, img, T, last, ex, bl);
+    const uint2* rg = (const uint2*)ranges;
+    auto kern = dg::k_render_fwd<B, PPT, false>;
+    const int R = resident_ctas(kern, B * B / PPT);
+    cudaMemsetAsync(w.hdr, 0, 256, s);
+    // automatic: split only when the tiles alone leave resident CTAs idle
+    // (with at least two tiles per CTA the persistent launch balances itself,
+    // and splitting costs the product pass)
+    const bool split = rv.total > 0 && (split_req > 0 || (split_req == 0 && rv.total < 2LL * R));
+    if (split) {
+        const dg::SplitCfg cfg{split_req, R, w.cap};
+        const long long n = rv.total;
+        const int nb = (int)((n + dg::SCAN_TILE - 1) / dg::SCAN_TILE);
+        dg::k_scan_reduce<<<nb, dg::SCAN_THREADS, 0, s>>>(dg::LoadLen{rg}, n, w.bsum);
+        dg::k_scan_top<<<1, 1024, 0, s>>>(w.bsum, nb, &w.hdr->M);
+        dg_note_launch(2);
+        dg::exclusive_scan(dg::LoadChunks{rg, w.hdr, cfg}, n, w.toff, w.bsum, &w.hdr->totals, s);
+        const int pg = (int)((n + 255) / 256);
+        dg::k_plan_items<<<pg < 1024 ? pg : 1024, 256, 0, s>>>(rg, (int)n, w.hdr, cfg, w.toff, w.items, w.sitems);
+        auto kprod = dg::k_render_fwd<B, PPT, true>;
+        kprod<<<resident_ctas(kprod, B * B / PPT), B * B / PPT, 0, s>>>(
+            (const float4*)feat, gid, rg, rv, w.hdr, w.items, w.sitems, w.sl, img, T, last, ex, bl);
+        dg_note_launch(2);
+    }
+    const int grid = split ? R : (R < rv.total ? R : (rv.total > 0 ? rv.total : 1));
+    kern<<<grid, B * B / PPT, 0, s>>>((const float4*)feat, gid, rg, rv, w.hdr, w.items, w.sitems, w.sl, img, T,
+                                      last, ex, bl);
     dg_note_launch();
+    if (split) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        dg::k_render_combine<B><<<4 * (sms > 0 ? sms : 1), B * B, 0, s>>>(rg, rv, w.hdr, w.sitems, w.sl, img, T,
+                                                                         last, ex, bl);
+        dg_note_launch();
+    }
+    return DG_OK;
 }
 
 template <int B, int PPT>
 static void launch_bwd(const float* feat, const uint32_t* gid, const uint32_t* ranges, const dg::RViews& rv,
-                       int* counter, const float* T, const int* last, const float* dL, float* g2, cudaStream_t s)
+                       const RenderWs& w, const float* T, const int* last, const float* dL, float* g2, cudaStream_t s)
 {
     auto kern = dg::k_render_bwd<B, PPT>;
-    const int grid = persistent_grid(kern, B * B / PPT, rv.total);
-    kern<<<grid, B * B / PPT, 0, s>>>((const float4*)feat, gid, (const uint2*)ranges, rv, counter, T, last, dL,
-                                      (float4*)g2);
+    const int grid = resident_ctas(kern, B * B / PPT);
+    cudaMemsetAsync(&w.hdr->cnt_bwd, 0, sizeof(int), s);
+    kern<<<grid, B * B / PPT, 0, s>>>((const float4*)feat, gid, (const uint2*)ranges, rv, w.hdr, w.items, w.sl, T,
+                                      last, dL, (float4*)g2);
     dg_note_launch();
 }
 
@@ -492,6 +815,14 @@ static int resolve_ppt(const dg_raster_opts* o, bool backward)
 
 bool dg_check_cameras(const dg_camera* cams, int n_views);
 
+static long long total_tiles(const dg_camera* cams, int n_views, int B)
+{
+    long long t = 0;
+    for (int v = 0; v < n_views; ++v)
+        t += (long long)((cams[v].width + B - 1) / B) * ((cams[v].height + B - 1) / B);
+    return t;
+}
+
 static bool render_args(const dg_camera* cams, int n_views, const dg_raster_opts* opts, void* ws, size_t ws_bytes)
 {
     if (!dg_check_cameras(cams, n_views)) return false;
@@ -499,11 +830,20 @@ static bool render_args(const dg_camera* cams, int n_views, const dg_raster_opts
     if (opts->tile != 8 && opts->tile != 16) { dg_set_error("render supports tile 8 or 16, got %d", opts->tile); return false; }
     const int p = opts->pixels_per_thread;
     if (p != 0 && p != 1 && p != 2 && p != 4) { dg_set_error("pixels_per_thread must be 0, 1, 2 or 4, got %d", p); return false; }
-    if (!ws || ws_bytes < dg_render_workspace_size()) { dg_set_error("render workspace missing or too small"); return false; }
+    if (total_tiles(cams, n_views, opts->tile) >= (1LL << 30)) { dg_set_error("too many tiles"); return false; }
+    const size_t need = dg_render_workspace_size(cams, n_views, opts);
+    if (!ws || ws_bytes < need) { dg_set_error("render workspace missing or too small (%zu < %zu bytes)", ws_bytes, need); return false; }
+    if (((uintptr_t)ws) & 255u) { dg_set_error("render workspace must be 256-byte aligned"); return false; }
     return true;
 }
 
-extern "C" size_t dg_render_workspace_size(void) { return 256; }
+extern "C" size_t dg_render_workspace_size(const dg_camera* cams, int32_t n_views, const dg_raster_opts* opts)
+{
+    if (!cams || !opts || n_views < 1 || n_views > DG_MAX_VIEWS || (opts->tile != 8 && opts->tile != 16)) return 0;
+    for (int v = 0; v < n_views; ++v)
+        if (cams[v].width <= 0 || cams[v].height <= 0) return 0;
+    return render_ws(nullptr, total_tiles(cams, n_views, opts->tile), opts->tile, opts->split_len >= 0).bytes;
+}
 
 extern "C" dg_status dg_render_fwd(const float* feat, const uint32_t* gid, const uint32_t* ranges,
                                    const dg_camera* cams, int32_t n_views, const dg_raster_opts* opts, float* img,
@@ -514,14 +854,15 @@ extern "C" dg_status dg_render_fwd(const float* feat, const uint32_t* gid, const
     if (!ranges || !img || !T_final || !last) { dg_set_error("null buffer"); return DG_ERR_ARG; }
     if (feat && (((uintptr_t)feat) & 15u)) { dg_set_error("feat must be 16-byte aligned"); return DG_ERR_ARG; }
     cudaStream_t s = (cudaStream_t)stream;
-    const dg::RViews rv = make_rviews(cams, n_views, opts->tile, opts);
-    int* counter = (int*)ws;
-    cudaMemsetAsync(counter, 0, sizeof(int), s);
+    const int B = opts->tile;
+    const dg::RViews rv = make_rviews(cams, n_views, B, opts);
+    const RenderWs w = render_ws(ws, rv.total, B, opts->split_len >= 0);
+    const int sp = opts->split_len;
     const int ppt = resolve_ppt(opts, false);
-    if (opts->tile == 8) launch_fwd<8, 1>(feat, gid, ranges, rv, counter, img, T_final, last, examined, blended, s);
-    else if (ppt == 1) launch_fwd<16, 1>(feat, gid, ranges, rv, counter, img, T_final, last, examined, blended, s);
-    else if (ppt == 2) launch_fwd<16, 2>(feat, gid, ranges, rv, counter, img, T_final, last, examined, blended, s);
-    else launch_fwd<16, 4>(feat, gid, ranges, rv, counter, img, T_final, last, examined, blended, s);
+    if (B == 8) launch_fwd<8, 1>(feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
+    else if (ppt == 1) launch_fwd<16, 1>(feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
+    else if (ppt == 2) launch_fwd<16, 2>(feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
+    else launch_fwd<16, 4>(feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
     return dg_check_launch("render_fwd");
 }
 
@@ -536,13 +877,13 @@ extern "C" dg_status dg_render_bwd(const float* feat, const uint32_t* gid, const
     if (grad2d && (((uintptr_t)grad2d) & 15u)) { dg_set_error("grad2d must be 16-byte aligned"); return DG_ERR_ARG; }
     cudaStream_t s = (cudaStream_t)stream;
     if (n_records > 0) cudaMemsetAsync(grad2d, 0, sizeof(float) * DG_FEAT_FLOATS * (size_t)n_records, s);
-    const dg::RViews rv = make_rviews(cams, n_views, opts->tile, opts);
-    int* counter = (int*)ws;
-    cudaMemsetAsync(counter, 0, sizeof(int), s);
+    const int B = opts->tile;
+    const dg::RViews rv = make_rviews(cams, n_views, B, opts);
+    const RenderWs w = render_ws(ws, rv.total, B, opts->split_len >= 0);
     const int ppt = resolve_ppt(opts, true);
-    if (opts->tile == 8) launch_bwd<8, 1>(feat, gid, ranges, rv, counter, T_final, last, dL_dimg, grad2d, s);
-    else if (ppt == 1) launch_bwd<16, 1>(feat, gid, ranges, rv, counter, T_final, last, dL_dimg, grad2d, s);
-    else if (ppt == 2) launch_bwd<16, 2>(feat, gid, ranges, rv, counter, T_final, last, dL_dimg, grad2d, s);
-    else launch_bwd<16, 4>(feat, gid, ranges, rv, counter, T_final, last, dL_dimg, grad2d, s);
+    if (B == 8) launch_bwd<8, 1>(feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
+    else if (ppt == 1) launch_bwd<16, 1>(feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
+    else if (ppt == 2) launch_bwd<16, 2>(feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
+    else launch_bwd<16, 4>(feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
     return dg_check_launch("render_bwd");
 }

@@ -58,7 +58,7 @@ class Rasterizer:
         self.M_cap = 0
         self.n_tiles = 0
         self.ws = None
-        self.rws = torch.empty(capi.dg_render_workspace_size(), dtype=torch.uint8, device=self.device)
+        self.rws = None  # render workspace, shared by a batch's forward and backward
         self.examined = None
         self.blended = None
         self.mark = None  # optional callback(stage_name) after each stage, for event timing
@@ -104,6 +104,11 @@ class Rasterizer:
             self.ranges = torch.empty((n_tiles, 2), dtype=torch.int32, device=self.device)
             self.n_tiles = n_tiles
 
+    def _ensure_rws(self, carr, V):
+        need = capi.dg_render_workspace_size(carr, V, self.opts_fwd)
+        if self.rws is None or self.rws.numel() < need:
+            self.rws = torch.empty(need, dtype=torch.uint8, device=self.device)
+
     # ------------------------------------------------------------ passes
     def forward(self, params: torch.Tensor, P: int, cams, stream=None, examined: bool = False) -> Frame:
         """Project, bin, sort and composite P Gaussians of the planar
@@ -143,6 +148,7 @@ class Rasterizer:
         if examined:
             ex = torch.empty(npix, dtype=torch.int32, device=self.device)
             bl = torch.empty(npix, dtype=torch.int32, device=self.device)
+        self._ensure_rws(carr, V)
         capi.dg_render_fwd(self.feat, self.gid, self.ranges, carr, V, self.opts_fwd, img, T, last, ex, bl,
                            self.rws, self.rws.numel(), stream)
         self._mark("render_fwd")
@@ -163,6 +169,27 @@ class Rasterizer:
             self.examined = exs[0] if V == 1 else exs
             self.blended = bls[0] if V == 1 else bls
         return fr
+
+    def backward_render(self, fr: Frame, dL_dimg: torch.Tensor, stream=None) -> None:
+        """Render adjoint only: fills self.grad2d (per-record 2D gradients)."""
+        stream = stream or torch.cuda.current_stream(self.device)
+        assert dL_dimg.is_contiguous() and dL_dimg.dtype == torch.float32
+        assert dL_dimg.numel() == fr.flat_img.numel()
+        carr = capi.cameras(fr.cams)
+        V = len(fr.cams)
+        capi.dg_render_bwd(self.feat, self.gid, self.ranges, carr, V, self.opts_bwd, fr.flat_T, fr.flat_last,
+                           dL_dimg, V * fr.P, self.grad2d, self.rws, self.rws.numel(), stream)
+        self._mark("render_bwd")
+
+    def project_bwd_adam(self, params: torch.Tensor, stride: int, fr: Frame, m, v, lr, step, beta1=0.9,
+                         beta2=0.999, eps=1e-15, grads=None, stream=None) -> None:
+        """Projection adjoint fused with the Adam update of params/m/v
+        (planar [59][stride] buffers holding at least fr.P Gaussians)."""
+        stream = stream or torch.cuda.current_stream(self.device)
+        carr = capi.cameras(fr.cams)
+        capi.dg_project_bwd_adam(params, stride, fr.P, carr, len(fr.cams), self.opts, self.radius, self.clamp,
+                                 self.grad2d, grads, m, v, lr, beta1, beta2, eps, step, stream)
+        self._mark("project_bwd_adam")
 
     def backward(self, params: torch.Tensor, fr: Frame, dL_dimg: torch.Tensor, grads: torch.Tensor,
                  stream=None) -> None:

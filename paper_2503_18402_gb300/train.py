@@ -30,6 +30,7 @@ import numpy as np
 import torch
 
 from . import capi
+from .autotune import RenderTuner, Shape
 from .raster import Rasterizer, make_camera
 from .schedule import spectrum_table
 
@@ -61,6 +62,16 @@ class TrainConfig:
     # the first opacity reset; off by default here because the synthetic ground
     # truth's Gaussians already have ~30 px radii at full resolution
     big_point_prune: bool = False
+    # scheduled arm: keep densifying until the first full-resolution iteration
+    # (Eq. 4 reaches P_fin there), so that the primitive growth curve spans the
+    # optimisation as the paper describes, instead of stopping at densify_until
+    densify_until_full: bool = True
+    # backbone loss (1 - lambda) L1 + lambda D-SSIM; 0 trains on L1 alone
+    ssim_lambda: float = 0.2
+    # render launch shape: chosen per (image size, P) bucket by timing, or fixed
+    autotune: bool = True
+    # projection adjoint fused with the Adam update (no stored gradient)
+    fused_adam: bool = True
     seed: int = 0
 
 
@@ -85,11 +96,13 @@ class Trainer:
         self.acc = torch.zeros(cap, **f32)
         self.den = torch.zeros(cap, **f32)
         self.maxr = torch.zeros(cap, **f32)
-        self.rz = Rasterizer(self.dev, capi.raster_opts())
+        self.tuner = RenderTuner(self.dev, capi.raster_opts(), fixed=None if cfg.autotune else Shape(16, 2, 4, 0))
+        self.rz = self.tuner.rasterizer(Shape(8, 1, 1, 0))  # evaluation renders
         n_full = 3 * self.H * self.W
         self.dL = torch.empty(n_full, **f32)
-        self.loss = torch.zeros(1, **f32)
+        self.loss = torch.zeros(2, **f32)
         self.lws = torch.empty(capi.dg_loss_workspace_size(n_full), dtype=torch.uint8, device=self.dev)
+        self.sws = torch.empty(capi.dg_ssim_workspace_size([(self.W, self.H)]), dtype=torch.uint8, device=self.dev)
         self.dws = None
         self.counts = torch.zeros(2, dtype=torch.int64, device=self.dev)
         self.P_out = torch.zeros(1, dtype=torch.int64, device=self.dev)
@@ -102,6 +115,7 @@ class Trainer:
         self.sched = None
         self.history = []
         self.init_schedule_s = 0.0
+        self.densify_until = cfg.densify_until
 
     # ---------------------------------------------------------------- schedule
     def init_schedule(self):
@@ -112,6 +126,8 @@ class Trainer:
                               P_cap=float(cfg.P_cap), lr_pos_init=cfg.lr_pos_init * cfg.extent,
                               lr_pos_final=cfg.lr_pos_final * cfg.extent)
         self.sched = capi.dg_schedule_init(sat, self.H, self.W, p)
+        if cfg.densify_until_full:
+            self.densify_until = max(cfg.densify_until, int(self.sched.k_full))
         torch.cuda.synchronize()
         self.init_schedule_s = time.perf_counter() - t0
 
@@ -155,18 +171,31 @@ class Trainer:
         j = self._next_view()
         cam = self._camera(j, h, w)
         params = b["p"][:, :P]
-        fr = self.rz.forward(params, P, cam, self.stream)
+        shape, rz, key = self.tuner.pick(h * w, P)
+        e0 = self.tuner.start(self.stream)
+        fr = rz.forward(params, P, cam, self.stream)
         n = 3 * h * w
-        capi.dg_loss_l1(fr.img, self._target(j, r, h, w), n, self.dL, self.loss, self.lws, self.lws.numel(), self.stream)
-        self.rz.backward(params, fr, self.dL[:n].view(3, h, w), self.grads[:, :P], self.stream)
-        if k < cfg.densify_until:
-            capi.dg_densify_stats(self.rz.grad2d, self.rz.radius, P, cam, 1, self.acc, self.den, self.maxr,
-                                  self.stream)
+        tgt = self._target(j, r, h, w)
+        if cfg.ssim_lambda > 0:
+            capi.dg_loss_l1_dssim(fr.img, tgt, [(w, h)], cfg.ssim_lambda, self.dL, self.loss, self.sws,
+                                  self.sws.numel(), self.stream)
+        else:
+            capi.dg_loss_l1(fr.img, tgt, n, self.dL, self.loss, self.lws, self.lws.numel(), self.stream)
+        rz.backward_render(fr, self.dL[:n].view(3, h, w), self.stream)
+        self.tuner.stop(key, shape, e0, self.stream)
+        if k < self.densify_until:
+            capi.dg_densify_stats(rz.grad2d, rz.radius, P, cam, 1, self.acc, self.den, self.maxr, self.stream)
         lr = [lr_pos] * 3 + [cfg.lr_scale] * 3 + [cfg.lr_rot] * 4 + [cfg.lr_opacity] + [cfg.lr_dc] * 3 + \
              [cfg.lr_rest] * 45
-        capi.dg_adam_step(b["p"], self.grads, b["m"], b["v"], self.cap, P, lr, 0.9, 0.999, 1e-15, k + 1, self.stream)
+        if cfg.fused_adam:
+            rz.project_bwd_adam(b["p"], self.cap, fr, b["m"], b["v"], lr, k + 1, stream=self.stream)
+        else:
+            capi.dg_project_bwd(params, self.cap, P, cam, 1, rz.opts, rz.radius, rz.clamp, rz.grad2d,
+                                self.grads[:, :P], self.stream)
+            capi.dg_adam_step(b["p"], self.grads, b["m"], b["v"], self.cap, P, lr, 0.9, 0.999, 1e-15, k + 1,
+                              self.stream)
         kk = k + 1
-        if cfg.densify_from <= kk <= cfg.densify_until and kk % cfg.densify_every == 0:
+        if cfg.densify_from <= kk <= self.densify_until and kk % cfg.densify_every == 0:
             self.densify(kk)
         if kk % cfg.opacity_reset_every == 0 and kk <= cfg.densify_until:
             b = self.buf[self.cur]
@@ -226,11 +255,12 @@ class Trainer:
             res_hist[r] = res_hist.get(r, 0) + 1
             if log_every and (k + 1) % log_every == 0:
                 torch.cuda.synchronize()
-                print(json.dumps(dict(iter=k + 1, P=self.P, r=r, loss=float(self.loss.item()),
+                print(json.dumps(dict(iter=k + 1, P=self.P, r=r, loss=float(self.loss[0].item()),
                                       s=round(time.perf_counter() - t0, 2))), flush=True)
         torch.cuda.synchronize()
         return dict(seconds=time.perf_counter() - t0, schedule_init_s=self.init_schedule_s, P_final=self.P,
-                    iters_per_factor={str(k): v for k, v in sorted(res_hist.items())})
+                    iters_per_factor={str(k): v for k, v in sorted(res_hist.items())},
+                    render_shapes=self.tuner.summary())
 
 
 def make_dataset(n_gt, n_views, W, H, device, seed=1001):
@@ -261,6 +291,8 @@ def main(argv=None):
     ap.add_argument("--height", type=int, default=822)
     ap.add_argument("--p-cap", type=int, default=3_000_000)
     ap.add_argument("--log-every", type=int, default=0)
+    ap.add_argument("--ssim-lambda", type=float, default=0.2)
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args(argv)
     from . import synth
     dev = torch.device("cuda")
@@ -269,7 +301,8 @@ def main(argv=None):
     arms = ["plain", "scheduled"] if args.arm == "both" else [args.arm]
     results = {}
     for arm in arms:
-        cfg = TrainConfig(iters=args.iters, scheduled=(arm == "scheduled"), P_cap=args.p_cap)
+        cfg = TrainConfig(iters=args.iters, scheduled=(arm == "scheduled"), P_cap=args.p_cap,
+                          ssim_lambda=args.ssim_lambda, autotune=not args.no_autotune)
         if args.iters < 30000:  # compress the backbone's iteration windows proportionally
             s = args.iters / 30000
             cfg.densify_from = max(1, int(500 * s)); cfg.densify_until = int(15000 * s)

@@ -234,6 +234,85 @@ def test_pixels_per_thread_variants(ppt, W, H):
     assert ok, (worst, nbad)
 
 
+# ---------------------------------------------------------------- split lists
+def _render_split(g, cam, tile, split, bg, ppt=None):
+    opts = capi.raster_opts(tile=tile, bg=bg, split_len=split)
+    rz = Rasterizer("cuda", opts, ppt_fwd=ppt, ppt_bwd=ppt)
+    params = G.gpu_params(g)
+    fr = rz.forward(params, g.shape[0], G.gpu_camera(cam), examined=True)
+    torch.cuda.synchronize()
+    return rz, params, fr
+
+
+@pytest.mark.parametrize("tile,ppt", [(8, None), (16, 1), (16, 2), (16, 4)])
+@pytest.mark.parametrize("split", [-1, 0, 16, 37, 100])
+def test_split_lists_match_oracle(tile, ppt, split):
+    """Chunked compositing (product pass, exact pass from the prefix product,
+    combine) gives the sequential Eq. 1 result: same last/examined/blended,
+    images and gradients within tolerance, for chunk lengths that do and do
+    not divide the batch size."""
+    W, H, n = 130, 99, 6000
+    g = synth.random_gaussians(n, 4242)
+    g[:, 3:6] += 0.3
+    cam = synth.camera_cfg0(W, H, 4.0)
+    bg = (0.3, 0.1, 0.2)
+    rz, params, fr = _render_split(g, cam, tile, split, bg, ppt)
+    k = oracle.consts(tile=tile)
+    rec = _records(rz, n)
+    gid, ranges = _gpu_bins(rz, fr)
+    orf = oracle.render_fwd(rec["feat"], W, H, tile, gid, ranges, G.f32(bg), k)
+    assert np.abs(G.np_(fr.img) - orf["img"]).max() <= 1e-5
+    assert np.abs(G.np_(fr.T) - orf["T"]).max() <= 1e-5
+    np.testing.assert_array_equal(G.np_(fr.last), orf["last"])
+    np.testing.assert_array_equal(G.np_(rz.examined), orf["examined"])
+    np.testing.assert_array_equal(G.np_(rz.blended), orf["blended"])
+    rng = np.random.default_rng(11)
+    dL = (rng.normal(size=(3, H, W)) / (3 * H * W)).astype(np.float32)
+    grads = torch.empty_like(params)
+    rz.backward(params, fr, torch.from_numpy(dL).cuda(), grads)
+    torch.cuda.synchronize()
+    og2 = oracle.render_bwd(rec["feat"], W, H, tile, gid, ranges, G.f32(bg), k, dL.astype(np.float64))
+    ok, worst, nbad = G.grad_close(G.np_(rz.grad2d[:n])[:, :9], og2)
+    assert ok, (worst, nbad)
+
+
+def test_split_low_resolution_long_lists():
+    """A low-resolution view of many Gaussians (thousands of entries per
+    tile, many pixels never reaching the stop threshold): automatic
+    splitting vs no splitting vs the oracle."""
+    W, H, n = 61, 41, 30000
+    g = synth.random_gaussians(n, 999)
+    g[:, 10] = -1.5  # low opacity: long compositing chains
+    cam = synth.camera_cfg0(W, H, 4.0)
+    bg = (0.0, 0.0, 0.0)
+    out = {}
+    for split in (-1, 0):
+        rz, params, fr = _render_split(g, cam, 8, split, bg)
+        rng = np.random.default_rng(5)
+        dL = (rng.normal(size=(3, H, W)) / (3 * H * W)).astype(np.float32)
+        grads = torch.empty_like(params)
+        rz.backward(params, fr, torch.from_numpy(dL).cuda(), grads)
+        torch.cuda.synchronize()
+        out[split] = (rz, fr, dL, G.np_(rz.grad2d[:n])[:, :9].copy(), G.np_(grads))
+    rz, fr, dL, g2, _ = out[0]
+    rz1, fr1, _, g21, _ = out[-1]
+    assert int(G.np_(rz.examined).max()) > 1000  # long chains are exercised
+    np.testing.assert_array_equal(G.np_(fr.last), G.np_(fr1.last))
+    np.testing.assert_array_equal(G.np_(rz.examined), G.np_(rz1.examined))
+    np.testing.assert_array_equal(G.np_(rz.blended), G.np_(rz1.blended))
+    assert np.abs(G.np_(fr.img) - G.np_(fr1.img)).max() <= 1e-5
+    k = oracle.consts(tile=8)
+    rec = _records(rz, n)
+    gid, ranges = _gpu_bins(rz, fr)
+    orf = oracle.render_fwd(rec["feat"], W, H, 8, gid, ranges, np.zeros(3), k)
+    assert np.abs(G.np_(fr.img) - orf["img"]).max() <= 1e-5
+    np.testing.assert_array_equal(G.np_(fr.last), orf["last"])
+    og2 = oracle.render_bwd(rec["feat"], W, H, 8, gid, ranges, np.zeros(3), k, dL.astype(np.float64))
+    for got in (g2, g21):
+        ok, worst, nbad = G.grad_close(got, og2)
+        assert ok, (worst, nbad)
+
+
 def test_empty_and_all_culled():
     cam = U.identity_cam(40, 24, 50.0)
     bg = (0.2, 0.5, 0.9)
@@ -321,6 +400,52 @@ def test_adam_parity():
     got = G.np_(tp)
     np.testing.assert_allclose(got[:, :P], op, rtol=1e-5, atol=1e-6)
     np.testing.assert_array_equal(got[:, P:], p[:, P:])  # padding untouched
+
+
+@pytest.mark.parametrize("sh,V", [(3, 1), (3, 3), (1, 2)])
+def test_fused_project_bwd_adam_matches_two_calls(sh, V):
+    """dg_project_bwd_adam gives the bits of dg_project_bwd followed by
+    dg_adam_step (including Gaussians culled in every view, whose moments
+    still decay)."""
+    g = synth.random_gaussians(3000, 21 + V)
+    g[:, 3:6] += 0.3
+    sizes = [(64, 64), (90, 50), (40, 70)][:V]
+    cams = [G.gpu_camera(synth.camera_cfg0(W, H, 4.0 + 0.7 * i)) for i, (W, H) in enumerate(sizes)]
+    opts = capi.raster_opts(sh_degree=sh)
+    rz = Rasterizer("cuda", opts)
+    P = g.shape[0]
+    stride = P + 13
+    base = np.zeros((59, stride), np.float32)
+    base[:, :P] = g.T
+    params = torch.from_numpy(base).cuda()
+    fr = rz.forward(params[:, :P], P, cams)
+    rng = np.random.default_rng(V)
+    dL = torch.from_numpy((rng.normal(size=fr.flat_img.numel()) / 1e4).astype(np.float32)).cuda()
+    rz.backward(params[:, :P], fr, dL, torch.empty_like(params[:, :P]))
+    lr = np.linspace(1e-4, 1e-2, 59).astype(np.float32)
+    m0 = torch.from_numpy(rng.normal(size=(59, stride)).astype(np.float32) * 1e-3).cuda()
+    v0 = torch.from_numpy(np.abs(rng.normal(size=(59, stride))).astype(np.float32) * 1e-6).cuda()
+    # two calls
+    p1, m1, v1 = params.clone(), m0.clone(), v0.clone()
+    grads = torch.zeros_like(params)
+    capi.dg_project_bwd(p1, stride, P, cams, V, opts, rz.radius, rz.clamp, rz.grad2d, grads)
+    capi.dg_adam_step(p1, grads, m1, v1, stride, P, lr, 0.9, 0.999, 1e-15, 7)
+    # fused, also writing the gradient
+    p2, m2, v2 = params.clone(), m0.clone(), v0.clone()
+    grads2 = torch.zeros_like(params)
+    capi.dg_project_bwd_adam(p2, stride, P, cams, V, opts, rz.radius, rz.clamp, rz.grad2d, grads2, m2, v2, lr, 0.9,
+                             0.999, 1e-15, 7)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(G.np_(grads2), G.np_(grads))
+    for a, b in ((p2, p1), (m2, m1), (v2, v1)):
+        np.testing.assert_array_equal(G.np_(a), G.np_(b))
+    assert (G.np_(rz.radius[: V * P]).reshape(V, P) == 0).all(axis=0).any()  # some Gaussians culled everywhere
+    # without the gradient output
+    p3, m3, v3 = params.clone(), m0.clone(), v0.clone()
+    capi.dg_project_bwd_adam(p3, stride, P, cams, V, opts, rz.radius, rz.clamp, rz.grad2d, None, m3, v3, lr, 0.9,
+                             0.999, 1e-15, 7)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(G.np_(p3), G.np_(p1))
 
 
 # ---------------------------------------------------------------- full size, sampled
