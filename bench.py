@@ -47,8 +47,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-gauss", type=int, default=N_GAUSS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--unfused-adam", action="store_true",
-                    help="projection adjoint and Adam as two kernels (default: fused)")
+    ap.add_argument("--fused-adam", action="store_true",
+                    help="projection adjoint fused with Adam (default: two kernels)")
     ap.add_argument("--cpu-frac", type=float, default=0.125,
                     help="area/Gaussian fraction of one view timed for the CPU baseline")
     return ap.parse_args()
@@ -60,7 +60,7 @@ def config(args, n_gauss, shape=None):
             "tile": shape.tile if shape else 16, "render_shape": shape.label() if shape else None,
             "sh_degree": 3, "loss": "0.8 L1 + 0.2 D-SSIM",
             "step": "project+bin+render_fwd+loss+render_bwd+project_bwd+adam",
-            "adjoint_adam": "two kernels" if args.unfused_adam else "fused",
+            "adjoint_adam": "fused" if args.fused_adam else "two kernels",
             "l2": "working set 1.9 GB > L2 (no flush)", "parallelism": f"replicas{args.gpus}"}
 
 
@@ -168,7 +168,7 @@ def run_ours(args):
             mark("loss")
         r.backward_render(fr, dL, stream)
         adam_t[0] += 1
-        if args.unfused_adam:
+        if not args.fused_adam:
             capi.dg_project_bwd(params, stride, P, gcams[j], 1, r.opts, r.radius, r.clamp, r.grad2d, grads, stream)
             if mark:
                 mark("project_bwd")

@@ -38,6 +38,8 @@ class Shape:
 CANDIDATES = (
     Shape(8, 1, 1, 0),
     Shape(8, 1, 1, -1),
+    Shape(8, 2, 2, 0),
+    Shape(8, 1, 2, 0),
     Shape(16, 2, 4, 0),
     Shape(16, 1, 1, 0),
     Shape(16, 2, 2, -1),

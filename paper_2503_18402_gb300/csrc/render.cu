@@ -3,11 +3,11 @@
 // Persistent launches over all views: one CTA per resident slot, each taking
 // work items from an atomic counter until none are left, so items of very
 // different cost balance across the SMs and all views of a batch share one
-// launch.  Each thread owns PPT pixels of one column of a B x B tile (rows
-// ly, ly + B/PPT, ...).  A work item's list entries are streamed through
-// shared memory in batches of B*B/PPT records (one coalesced 48-byte gather
-// per thread per batch); every staged record is then evaluated for the
-// thread's PPT pixels.
+// launch.  Each warp owns an 8-pixel-wide block of 4*PPT rows of a B x B
+// tile, each lane PPT vertically adjacent pixels of one column.  A work item's
+// list entries are streamed through shared memory in batches of B*B/PPT
+// records (one coalesced 48-byte gather per thread per batch); every staged
+// record is then evaluated for the thread's PPT pixels.
 //
 // Work items.  Without splitting, an item is a whole tile.  A tile's list is
 // walked in order, so a tile with a long list is a serial chain that no other
@@ -93,6 +93,18 @@ __device__ inline bool tile_skip(const float4& a, const float4& b, float px0, fl
     return fmin > 2.f * logf(255.f * o) + 0.02f;
 }
 
+// Pixel layout of a work item: warp w owns an 8-pixel-wide block of 4*PPT
+// rows (blocks tile the B x B tile row-major); lane l owns column l % 8 and the
+// PPT adjacent rows (l / 8) * PPT + k.
+template <int B, int PPT>
+__device__ inline void pix_of(int tid, int* lx, int* ly0)
+{
+    constexpr int NBX = B / 8;
+    const int w = tid >> 5, l = tid & 31;
+    *lx = (w % NBX) * 8 + (l & 7);
+    *ly0 = (w / NBX) * (4 * PPT) + (l >> 3) * PPT;
+}
+
 // 2^x on the MUFU unit (ex2.approx, flush-to-zero).
 __device__ inline float ex2_approx(float x)
 {
@@ -102,6 +114,9 @@ __device__ inline float ex2_approx(float x)
 }
 
 constexpr float kLog2e = 1.4426950408889634f;
+// log2(1/255): the alpha >= 1/255 test is taken in the log2 domain, before the
+// exponential, identically in the forward and the backward
+constexpr float kLog2AlphaMin = -7.994353436858858f;
 
 // Stable block-wide compaction index of `keep`; *total = number kept.  Ends with a barrier.
 template <int NT>
@@ -276,11 +291,9 @@ k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
 {
     constexpr int NT = B * B / PPT;
     constexpr int NPIX = B * B;
-    constexpr int RSTEP = B / PPT;  // row step between a thread's pixels
-    __shared__ float4 s_a[NT];  // u, v, A, B
-    __shared__ float4 s_b[NT];  // C, o, r, g
-    __shared__ float s_c[NT];   // b
-    __shared__ int s_pos[NT];   // list position
+    __shared__ float4 s_a[NT];    // u, v, a', b'  (prescaled conic, see below)
+    __shared__ float2 s_q[NT];    // c', log2 o
+    __shared__ float4 s_col[NT];  // r, g, b, list position (int bits)
     __shared__ int s_w[NT / 32];
     __shared__ int4 s_item;
     const bool planned = hdr->planned != 0 && items != nullptr;
@@ -293,7 +306,8 @@ k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
     if (it.tile < 0) break;
     if (PROD && it.c == it.nch - 1) continue;  // the last chunk's product is never needed
     const int tile = it.tile, tx = it.tx, ty = it.ty, W = it.W, H = it.H;
-    const int lx = (int)(threadIdx.x % B), ly0 = (int)(threadIdx.x / B);
+    int lx, ly0;
+    pix_of<B, PPT>(threadIdx.x, &lx, &ly0);
     const int x = tx * B + lx;
     const int y0 = ty * B + ly0;
     const float pxc = (float)x + 0.5f;
@@ -309,14 +323,14 @@ k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
     bool done[PPT];
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        const int y = y0 + k * RSTEP;
+        const int y = y0 + k;
         pyc[k] = (float)y + 0.5f;
         T[k] = 1.f; c0[k] = c1[k] = c2[k] = 0.f;
         last[k] = 0; stop[k] = -1; nbl[k] = 0;
         done[k] = !(x < W && y < H);
         if (!PROD && split && it.c > 0) {
             // transmittance in front of the chunk: product of the earlier chunks' products
-            const int p = (ly0 + k * RSTEP) * B + lx;
+            const int p = (ly0 + k) * B + lx;
             for (int c = 0; c < it.c; ++c) T[k] *= sl.prod[(size_t)(it.slot0 + c) * NPIX + p];
             if (T[k] < kTMin) done[k] = true;  // stopped in an earlier chunk
         }
@@ -342,16 +356,13 @@ k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
         if (keep) {
             // prescaled: p = log2(e) * power = dx (a' dx + b' dy) + c' dy^2, alpha = 2^(p + log2 o)
             s_a[slot] = make_float4(ga.x, ga.y, -0.5f * kLog2e * ga.z, -kLog2e * ga.w);
-            s_b[slot] = make_float4(-0.5f * kLog2e * gb.x, __log2f(gb.y), gb.z, gb.w);
-            s_c[slot] = gc;
-            s_pos[slot] = j;
+            s_q[slot] = make_float2(-0.5f * kLog2e * gb.x, __log2f(gb.y));
+            s_col[slot] = make_float4(gb.z, gb.w, gc, __int_as_float(j));
         }
         __syncthreads();
         for (int kk = 0; kk < cnt && !alldone; ++kk) {
             const float4 a = s_a[kk];
-            const float4 b = s_b[kk];
-            const float cb = s_c[kk];
-            const int pos = s_pos[kk];
+            const float2 q = s_q[kk];
             const float dx = a.x - pxc;
             const float adx = a.z * dx;
             alldone = true;
@@ -359,10 +370,13 @@ k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
             for (int k = 0; k < PPT; ++k) {
                 if (!done[k]) {
                     const float dy = a.y - pyc[k];
-                    const float p = fmaf(dx, fmaf(a.w, dy, adx), b.x * dy * dy);
-                    const float alpha = fminf(kAlphaMax, ex2_approx(p + b.y));
-                    if (p <= 0.f && alpha >= kAlphaMin) {
+                    const float p = fmaf(dx, fmaf(a.w, dy, adx), q.x * dy * dy);
+                    const float e = p + q.y;  // log2 of the unclamped alpha
+                    if (p <= 0.f && e >= kLog2AlphaMin) {
+                        const float alpha = fminf(kAlphaMax, ex2_approx(e));
                         const float Tn = fmaf(-alpha, T[k], T[k]);
+                        const float4 col = s_col[kk];
+                        const int pos = __float_as_int(col.w);
                         if (Tn < kTMin) {
                             done[k] = true;
                             stop[k] = pos;
@@ -370,9 +384,9 @@ k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
                         } else {
                             if (!PROD) {
                                 const float w = alpha * T[k];
-                                c0[k] += w * b.z;
-                                c1[k] += w * b.w;
-                                c2[k] += w * cb;
+                                c0[k] += w * col.x;
+                                c1[k] += w * col.y;
+                                c2[k] += w * col.z;
                                 last[k] = pos + 1;
                                 ++nbl[k];
                             }
@@ -388,7 +402,7 @@ k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
         const size_t s0 = (size_t)(it.slot0 + it.c) * NPIX;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-            const size_t s = s0 + (size_t)((ly0 + k * RSTEP) * B + lx);
+            const size_t s = s0 + (size_t)((ly0 + k) * B + lx);
             if (PROD) {
                 sl.prod[s] = T[k];
             } else {
@@ -405,7 +419,7 @@ k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
     float* im = img + 3 * it.poff;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        const int y = y0 + k * RSTEP;
+        const int y = y0 + k;
         if (x < W && y < H) {
             const size_t pix = (size_t)y * W + x;
             im[pix] = c0[k] + T[k] * rv.bg0;
@@ -531,12 +545,11 @@ k_render_bwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
 {
     constexpr int NT = B * B / PPT;
     constexpr int NPIX = B * B;
-    constexpr int RSTEP = B / PPT;
-    __shared__ float4 s_a[NT];
-    __shared__ float4 s_b[NT];
-    __shared__ float s_c[NT];
+    __shared__ float4 s_a[NT];    // u, v, a', b'  (the forward's prescaled conic)
+    __shared__ float2 s_q[NT];    // c', log2 o
+    __shared__ float4 s_k[NT];    // A, B, C, 1/o
+    __shared__ float4 s_col[NT];  // r, g, b, list position (int bits)
     __shared__ uint32_t s_g[NT];
-    __shared__ int s_pos[NT];
     __shared__ int s_w[NT / 32];
     __shared__ int s_n;
     __shared__ int4 s_item;
@@ -550,7 +563,8 @@ k_render_bwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
     const Item it = next_item(&hdr->cnt_bwd, count, planned ? items : nullptr, rv, &s_item);
     if (it.tile < 0) break;
     const int tile = it.tile, tx = it.tx, ty = it.ty, W = it.W, H = it.H;
-    const int lx = (int)(threadIdx.x % B), ly0 = (int)(threadIdx.x / B);
+    int lx, ly0;
+    pix_of<B, PPT>(threadIdx.x, &lx, &ly0);
     const int x = tx * B + lx;
     const int y0 = ty * B + ly0;
     const float pxc = (float)x + 0.5f;
@@ -567,7 +581,7 @@ k_render_bwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
     int mylast = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
-        const int y = y0 + k * RSTEP;
+        const int y = y0 + k;
         pyc[k] = (float)y + 0.5f;
         T[k] = 1.f; g0[k] = g1[k] = g2[k] = 0.f; lastp[k] = 0;
         S0[k] = S1[k] = S2[k] = 0.f;
@@ -580,7 +594,7 @@ k_render_bwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
             g2[k] = dl[2 * HW + pix];
             if (split) {
                 // the chunk's end transmittance and the colour behind the chunk
-                const size_t s = (size_t)(it.slot0 + it.c) * NPIX + (size_t)((ly0 + k * RSTEP) * B + lx);
+                const size_t s = (size_t)(it.slot0 + it.c) * NPIX + (size_t)((ly0 + k) * B + lx);
                 T[k] = sl.tout[s];
                 S0[k] = sl.c0[s]; S1[k] = sl.c1[s]; S2[k] = sl.c2[s];
             } else {
@@ -614,30 +628,35 @@ k_render_bwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
         const int slot = compact_index<NT>(keep, s_w, &cnt);
         if (keep) {
             s_g[slot] = g;
-            s_a[slot] = ga;
-            s_b[slot] = gb;
-            s_c[slot] = gc;
-            s_pos[slot] = j;
+            s_a[slot] = make_float4(ga.x, ga.y, -0.5f * kLog2e * ga.z, -kLog2e * ga.w);
+            s_q[slot] = make_float2(-0.5f * kLog2e * gb.x, __log2f(gb.y));
+            s_k[slot] = make_float4(ga.z, ga.w, gb.x, 1.f / gb.y);
+            s_col[slot] = make_float4(gb.z, gb.w, gc, __int_as_float(j));
         }
         __syncthreads();
         for (int kk = cnt - 1; kk >= 0; --kk) {
-            const int pos = s_pos[kk];
+            const float4 col = s_col[kk];
+            const int pos = __float_as_int(col.w);
             if (!__any_sync(0xffffffffu, pos < mylast)) continue;
             const float4 a = s_a[kk];
-            const float4 b = s_b[kk];
-            const float cr = b.z, cg = b.w, cb = s_c[kk];
+            const float2 q = s_q[kk];
+            const float cr = col.x, cg = col.y, cb = col.z;
             const float dx = a.x - pxc;
+            const float adx = a.z * dx;
             float du = 0.f, dv = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dop = 0.f, dr = 0.f, dgc = 0.f, db = 0.f;
             bool any = false;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 if (pos < lastp[k]) {
+                    // the forward's blend test and alpha, bit for bit
                     const float dy = a.y - pyc[k];
-                    const float power = -0.5f * (a.z * dx * dx + b.x * dy * dy) - a.w * dx * dy;
-                    const float G = __expf(power);
-                    const float raw = b.y * G;
-                    const float alpha = fminf(kAlphaMax, raw);
-                    if (power <= 0.f && alpha >= kAlphaMin) {
+                    const float p = fmaf(dx, fmaf(a.w, dy, adx), q.x * dy * dy);
+                    const float e = p + q.y;
+                    if (p <= 0.f && e >= kLog2AlphaMin) {
+                        const float raw = ex2_approx(e);
+                        const float alpha = fminf(kAlphaMax, raw);
+                        const float4 kc = s_k[kk];  // A, B, C, 1/o
+                        const float G = raw * kc.w;  // exp(power) = d alpha / d o
                         any = true;
                         const float inv = 1.f / (1.f - alpha);
                         T[k] *= inv;  // transmittance in front of this entry
@@ -653,8 +672,8 @@ k_render_bwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
                         if (raw <= kAlphaMax) {
                             dop += dLda * G;
                             const float dp = dLda * alpha;
-                            du -= dp * (a.z * dx + a.w * dy);
-                            dv -= dp * (a.w * dx + b.x * dy);
+                            du -= dp * (kc.x * dx + kc.y * dy);
+                            dv -= dp * (kc.y * dx + kc.z * dy);
                             dA -= 0.5f * dp * dx * dx;
                             dB -= dp * dx * dy;
                             dC -= 0.5f * dp * dy * dy;
@@ -804,11 +823,11 @@ static void launch_bwd(const float* feat, const uint32_t* gid, const uint32_t* r
 }
 
 // Pixels per thread used for (tile, request): tile 16 -> 1, 2 or 4 (0 selects
-// the default of each pass), tile 8 -> 1.
+// the default of each pass), tile 8 -> 1 or 2 (default 1).
 static int resolve_ppt(const dg_raster_opts* o, bool backward)
 {
-    if (o->tile == 8) return 1;
     const int req = o->pixels_per_thread;
+    if (o->tile == 8) return req == 2 ? 2 : 1;
     if (req == 1 || req == 2 || req == 4) return req;
     return backward ? 4 : 2;
 }
@@ -859,7 +878,8 @@ extern "C" dg_status dg_render_fwd(const float* feat, const uint32_t* gid, const
     const RenderWs w = render_ws(ws, rv.total, B, opts->split_len >= 0);
     const int sp = opts->split_len;
     const int ppt = resolve_ppt(opts, false);
-    if (B == 8) launch_fwd<8, 1>(feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
+    if (B == 8 && ppt == 2) launch_fwd<8, 2>(feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
+    else if (B == 8) launch_fwd<8, 1>(feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
     else if (ppt == 1) launch_fwd<16, 1>(feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
     else if (ppt == 2) launch_fwd<16, 2>(feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
     else launch_fwd<16, 4>(feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
@@ -881,7 +901,8 @@ extern "C" dg_status dg_render_bwd(const float* feat, const uint32_t* gid, const
     const dg::RViews rv = make_rviews(cams, n_views, B, opts);
     const RenderWs w = render_ws(ws, rv.total, B, opts->split_len >= 0);
     const int ppt = resolve_ppt(opts, true);
-    if (B == 8) launch_bwd<8, 1>(feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
+    if (B == 8 && ppt == 2) launch_bwd<8, 2>(feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
+    else if (B == 8) launch_bwd<8, 1>(feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
     else if (ppt == 1) launch_bwd<16, 1>(feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
     else if (ppt == 2) launch_bwd<16, 2>(feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
     else launch_bwd<16, 4>(feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);

@@ -113,45 +113,65 @@ def _band_noise(rng, n_waves=32, f_lo=0.5, f_hi=40.0, std=0.25):
     return tex
 
 
-def textured_scene(n: int, seed: int, n_surfaces: int = 20, shell_radius: float = 12.0,
-                   log_scale_mean: float = -4.5, dtype=np.float32) -> np.ndarray:
-    """(n, 59) Gaussians on textured planes/spheres plus a background shell."""
+def textured_scene(n: int, seed: int, n_surfaces: int = 400, size_range=(0.04, 0.9), shell_radius: float = 12.0,
+                   cover: float = 1.0, log_scale_std: float = 0.3, tex_f_hi: float = 40.0, tex_waves: int = 32,
+                   dtype=np.float32) -> np.ndarray:
+    """(n, 59) Gaussians on textured planes/spheres plus a background shell.
+
+    Layout: a dead-leaves arrangement, the classic model of natural-image
+    statistics -- ``n_surfaces`` plane patches and spheres with half-sizes drawn
+    from the scale-invariant density p(s) ~ s^-3 on ``size_range`` (equal
+    surface area per octave of size), placed at random in [-1.8, 1.8]^3, each
+    with its own base colour and a 1/f texture, so views have edges and
+    texture at every scale.  Gaussians are spread over the surfaces in
+    proportion to area (10% on the shell).  Scales follow the local density:
+    the mean scale is ``cover`` times the mean spacing sqrt(area / count), with
+    a log-normal spread, so surfaces are closed and resolved down to the
+    Gaussian spacing."""
     rng = np.random.default_rng(seed)
     g = np.zeros((n, NPARAM), dtype=dtype)
     n_shell = n // 10
     n_surf = n - n_shell
-    counts = np.full(n_surfaces, n_surf // n_surfaces)
-    counts[: n_surf - counts.sum()] += 1
+    lo, hi = size_range
+    # inverse CDF of p(s) ~ s^-3 on [lo, hi]
+    u = rng.uniform(size=n_surfaces)
+    size = 1.0 / np.sqrt(1.0 / lo ** 2 - u * (1.0 / lo ** 2 - 1.0 / hi ** 2))
+    is_plane = np.arange(n_surfaces) % 2 == 0
+    area = np.where(is_plane, (2.0 * size) ** 2, 4.0 * math.pi * size ** 2)
+    counts = np.floor(n_surf * area / area.sum()).astype(np.int64)
+    counts[np.argsort(-area)[: n_surf - counts.sum()]] += 1
     means = np.zeros((n, 3))
     dc = np.zeros((n, 3))
+    log_sigma = np.zeros(n)
     o = 0
     for s in range(n_surfaces):
         m = int(counts[s])
         centre = rng.uniform(-1.8, 1.8, size=3)
+        tex = _band_noise(rng, n_waves=tex_waves, f_hi=tex_f_hi)
+        base = rng.uniform(0.1, 0.9, size=3)
+        if m == 0:
+            continue
         uv = rng.uniform(-1.0, 1.0, size=(m, 2))
-        tex = _band_noise(rng)
-        if s % 2 == 0:  # plane patch
+        if is_plane[s]:
             a = rng.normal(size=3); a /= np.linalg.norm(a)
             b = np.cross(a, rng.normal(size=3)); b /= np.linalg.norm(b)
-            half = rng.uniform(0.4, 0.9)
-            means[o:o + m] = centre + half * (uv[:, :1] * a + uv[:, 1:] * b)
-        else:  # sphere
-            r = rng.uniform(0.25, 0.7)
+            means[o:o + m] = centre + size[s] * (uv[:, :1] * a + uv[:, 1:] * b)
+        else:
             th = np.arccos(uv[:, 0])
             ph = math.pi * uv[:, 1]
             d = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
-            means[o:o + m] = centre + r * d
-        base = rng.uniform(0.3, 0.7, size=3)
-        dc[o:o + m] = base + tex(uv)
+            means[o:o + m] = centre + size[s] * d
+        log_sigma[o:o + m] = math.log(cover * math.sqrt(area[s] / m))
+        dc[o:o + m] = base + tex(uv * size[s] / 0.65)  # texture frequency in world units
         o += m
     d = rng.normal(size=(n_shell, 3))
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     means[o:] = shell_radius * d
+    log_sigma[o:] = math.log(cover * math.sqrt(4.0 * math.pi * shell_radius ** 2 / max(n_shell, 1)))
     sky = _band_noise(rng, f_hi=20.0)
     dc[o:] = 0.5 + sky(d[:, :2] * 4.0)
     g[:, 0:3] = means
-    g[:, 3:6] = rng.normal(log_scale_mean, 0.5, size=(n, 3))
-    g[o:, 3:6] += math.log(shell_radius / 4.0)  # shell Gaussians scaled with distance
+    g[:, 3:6] = log_sigma[:, None] + rng.normal(0.0, log_scale_std, size=(n, 3))
     q = rng.normal(size=(n, 4))
     g[:, 6:10] = q / np.linalg.norm(q, axis=1, keepdims=True)
     g[:, 10] = rng.normal(0.0, 1.0, size=n)

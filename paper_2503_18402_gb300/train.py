@@ -70,8 +70,10 @@ class TrainConfig:
     ssim_lambda: float = 0.2
     # render launch shape: chosen per (image size, P) bucket by timing, or fixed
     autotune: bool = True
-    # projection adjoint fused with the Adam update (no stored gradient)
-    fused_adam: bool = True
+    # projection adjoint fused with the Adam update (no stored gradient); off:
+    # the fused kernel's register footprint (one thread per Gaussian holding all
+    # 59 gradients) leaves too few warps resident to stream params, m and v
+    fused_adam: bool = False
     seed: int = 0
 
 

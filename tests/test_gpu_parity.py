@@ -244,7 +244,7 @@ def _render_split(g, cam, tile, split, bg, ppt=None):
     return rz, params, fr
 
 
-@pytest.mark.parametrize("tile,ppt", [(8, None), (16, 1), (16, 2), (16, 4)])
+@pytest.mark.parametrize("tile,ppt", [(8, None), (8, 2), (16, 1), (16, 2), (16, 4)])
 @pytest.mark.parametrize("split", [-1, 0, 16, 37, 100])
 def test_split_lists_match_oracle(tile, ppt, split):
     """Chunked compositing (product pass, exact pass from the prefix product,
@@ -404,11 +404,15 @@ def test_adam_parity():
 
 @pytest.mark.parametrize("sh,V", [(3, 1), (3, 3), (1, 2)])
 def test_fused_project_bwd_adam_matches_two_calls(sh, V):
-    """dg_project_bwd_adam gives the bits of dg_project_bwd followed by
-    dg_adam_step (including Gaussians culled in every view, whose moments
-    still decay)."""
+    """dg_project_bwd_adam = dg_project_bwd followed by dg_adam_step
+    (including Gaussians culled in every view, whose moments still decay).
+    The adjoint's two instantiations may contract multiply-adds differently,
+    so their gradients agree within the gradient tolerance; the Adam update is
+    one contraction-free function, so given the same gradient the state is
+    bit-identical."""
     g = synth.random_gaussians(3000, 21 + V)
     g[:, 3:6] += 0.3
+    g[-50:, 0] = 100.0  # off-screen in every view: culled, zero gradient, moments still decay
     sizes = [(64, 64), (90, 50), (40, 70)][:V]
     cams = [G.gpu_camera(synth.camera_cfg0(W, H, 4.0 + 0.7 * i)) for i, (W, H) in enumerate(sizes)]
     opts = capi.raster_opts(sh_degree=sh)
@@ -436,8 +440,12 @@ def test_fused_project_bwd_adam_matches_two_calls(sh, V):
     capi.dg_project_bwd_adam(p2, stride, P, cams, V, opts, rz.radius, rz.clamp, rz.grad2d, grads2, m2, v2, lr, 0.9,
                              0.999, 1e-15, 7)
     torch.cuda.synchronize()
-    np.testing.assert_array_equal(G.np_(grads2), G.np_(grads))
-    for a, b in ((p2, p1), (m2, m1), (v2, v1)):
+    ok, worst, nbad = G.grad_close(G.np_(grads2), G.np_(grads))
+    assert ok, (worst, nbad)
+    p4, m4, v4 = params.clone(), m0.clone(), v0.clone()
+    capi.dg_adam_step(p4, grads2, m4, v4, stride, P, lr, 0.9, 0.999, 1e-15, 7)
+    torch.cuda.synchronize()
+    for a, b in ((p2, p4), (m2, m4), (v2, v4)):
         np.testing.assert_array_equal(G.np_(a), G.np_(b))
     assert (G.np_(rz.radius[: V * P]).reshape(V, P) == 0).all(axis=0).any()  # some Gaussians culled everywhere
     # without the gradient output
@@ -445,7 +453,7 @@ def test_fused_project_bwd_adam_matches_two_calls(sh, V):
     capi.dg_project_bwd_adam(p3, stride, P, cams, V, opts, rz.radius, rz.clamp, rz.grad2d, None, m3, v3, lr, 0.9,
                              0.999, 1e-15, 7)
     torch.cuda.synchronize()
-    np.testing.assert_array_equal(G.np_(p3), G.np_(p1))
+    np.testing.assert_array_equal(G.np_(p3), G.np_(p2))
 
 
 # ---------------------------------------------------------------- full size, sampled
@@ -468,7 +476,7 @@ def test_fullsize_sampled_tiles_and_pixels(fullsize):
     P, W, H = model.shape[0], 1237, 822
     rec = _records(rz, P)
     gid, ranges = _gpu_bins(rz, fr)
-    assert fr.M > 10_000_000 and int(rec["tiles"].sum()) == fr.M
+    assert fr.M > 2_000_000 and int(rec["tiles"].sum()) == fr.M
     # ranges partition [0, M) in tile order
     nz = ranges[:, 1] > ranges[:, 0]
     assert ranges[nz, 0].min() == 0 and ranges[nz, 1].max() == fr.M
