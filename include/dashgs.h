@@ -117,7 +117,12 @@ DG_API int64_t dg_kernel_launches(void);
  * tiles are ids toff[v] .. toff[v+1]-1 with toff the running sum of
  * ceil(W_v/B) * ceil(H_v/B).  Per-pixel arrays concatenate the views: images
  * [v][3][H_v][W_v] from element 3 * poff[v], T/last from poff[v], poff the
- * running sum of W_v * H_v. */
+ * running sum of W_v * H_v.
+ * cams_dev (projection and its adjoint): nullable device copy of the same
+ * n_views cameras.  When given, the kernels read each camera's pose and
+ * intrinsics from it when they run (so a call captured once in a CUDA graph
+ * can be replayed with new cameras written to that buffer); the image sizes
+ * and tile grids are always those of the host array. */
 
 /* Projection (EWA splatting of Sec. 3, "2D Gaussian splatted to the image
  * plane", and the SH colour of the colour coefficients c_i).
@@ -134,8 +139,8 @@ DG_API int64_t dg_kernel_launches(void);
  * Errors: DG_ERR_ARG for null pointers, P < 0, stride < P, sh_degree
  * outside 0..3, tile < 1, non-positive image size or focal length. */
 DG_API dg_status dg_project(const float* params, int64_t stride, int64_t P, const dg_camera* cams,
-                     int32_t n_views, const dg_raster_opts* opts, float* feat, float* depth, int32_t* radius,
-                     int32_t* tiles, uint8_t* clamp, dg_stream stream);
+                     const dg_camera* cams_dev, int32_t n_views, const dg_raster_opts* opts, float* feat,
+                     float* depth, int32_t* radius, int32_t* tiles, uint8_t* clamp, dg_stream stream);
 
 /* ---------------------------------------------------------------------- */
 /* Tile binning and ordering (the tile-based "GPU-friendly rendering
@@ -209,8 +214,9 @@ DG_API dg_status dg_render_bwd(const float* feat, const uint32_t* gid, const uin
  * Out: grads [59][stride] planar float32, overwritten for Gaussians 0..P-1
  *      (zero where culled in every view; rows above the SH degree are zero). */
 DG_API dg_status dg_project_bwd(const float* params, int64_t stride, int64_t P, const dg_camera* cams,
-                         int32_t n_views, const dg_raster_opts* opts, const int32_t* radius, const uint8_t* clamp,
-                         const float* grad2d, float* grads, dg_stream stream);
+                         const dg_camera* cams_dev, int32_t n_views, const dg_raster_opts* opts,
+                         const int32_t* radius, const uint8_t* clamp, const float* grad2d, float* grads,
+                         dg_stream stream);
 
 /* dg_project_bwd fused with dg_adam_step: the gradient of each parameter row
  * goes straight into the Adam update of that row (same arithmetic and result
@@ -219,10 +225,10 @@ DG_API dg_status dg_project_bwd(const float* params, int64_t stride, int64_t P, 
  * Gaussian).  grads: nullable; when given, the gradient is also written there.
  * params, m, v: planar [59][stride], updated in place; lr: host float[59]. */
 DG_API dg_status dg_project_bwd_adam(float* params, int64_t stride, int64_t P, const dg_camera* cams,
-                                     int32_t n_views, const dg_raster_opts* opts, const int32_t* radius,
-                                     const uint8_t* clamp, const float* grad2d, float* grads, float* m, float* v,
-                                     const float* lr, float beta1, float beta2, float eps, int64_t step,
-                                     dg_stream stream);
+                                     const dg_camera* cams_dev, int32_t n_views, const dg_raster_opts* opts,
+                                     const int32_t* radius, const uint8_t* clamp, const float* grad2d, float* grads,
+                                     float* m, float* v, const float* lr, float beta1, float beta2, float eps,
+                                     int64_t step, dg_stream stream);
 
 /* ---------------------------------------------------------------------- */
 /* L1 photometric loss of the 3DGS backbone the paper keeps (Sec. 5):
@@ -284,6 +290,29 @@ DG_API dg_status dg_loss_l1_noalloc(const float* img, const float* target, int64
 DG_API dg_status dg_adam_step(float* params, const float* grads, float* m, float* v, int64_t stride,
                        int64_t P, const float* lr, float beta1, float beta2, float eps,
                        int64_t step, dg_stream stream);
+
+/* Adam hyper-parameters of one step, in the layout the kernels read: per-row
+ * learning rates, betas, bias corrections bc1 = 1 - beta1^step and
+ * bc2_sqrt = sqrt(1 - beta2^step) (computed in FP64, rounded once), eps. */
+typedef struct dg_adam_hparams {
+    float lr[DG_NPARAM];
+    float beta1, beta2;
+    float bc1, bc2_sqrt;
+    float eps;
+} dg_adam_hparams;
+
+/* Host: fills *out for step `step` (>= 1) exactly as dg_adam_step uses it. */
+DG_API dg_status dg_adam_hparams_fill(const float* lr, float beta1, float beta2, float eps, int64_t step,
+                                      dg_adam_hparams* out);
+
+/* dg_adam_step with the hyper-parameters read from device memory at execution
+ * time (hp_dev: one dg_adam_hparams), for a step captured once in a CUDA graph
+ * and replayed with a new learning rate and step count.  skip_if: nullable
+ * device int32; when it holds a non-zero value (e.g. the binning status of the
+ * same step reporting a pair-list overflow) the update is skipped. */
+DG_API dg_status dg_adam_step_dev(float* params, const float* grads, float* m, float* v, int64_t stride,
+                                  int64_t P, const dg_adam_hparams* hp_dev, const int32_t* skip_if,
+                                  dg_stream stream);
 
 /* ---------------------------------------------------------------------- */
 /* Scheduled densification (supplementary "Densification of DashGaussian"):

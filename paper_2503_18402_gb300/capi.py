@@ -26,7 +26,7 @@ MAX_VIEWS = 16
 EXPORTS = ("dg_last_error", "dg_abi_version", "dg_kernel_launches", "dg_project", "dg_bin_workspace_size", "dg_bin_count",
            "dg_bin_sort", "dg_render_workspace_size", "dg_render_fwd", "dg_render_bwd", "dg_project_bwd", "dg_project_bwd_adam",
            "dg_loss_workspace_size", "dg_ssim_workspace_size", "dg_loss_l1_dssim",
-           "dg_loss_l1", "dg_loss_l1_noalloc", "dg_adam_step", "dg_spectrum_workspace_size",
+           "dg_loss_l1", "dg_loss_l1_noalloc", "dg_adam_step", "dg_adam_hparams_fill", "dg_adam_step_dev", "dg_spectrum_workspace_size",
            "dg_spectrum_accumulate", "dg_spectrum_finalize", "dg_downsample_area", "dg_schedule_init",
            "dg_schedule_step", "dg_schedule_densify", "dg_densify_stats", "dg_densify_workspace_size",
            "dg_densify_mark", "dg_densify_apply", "dg_mse", "dg_opacity_reset")
@@ -121,15 +121,15 @@ _SIGS = {
     "dg_last_error": ([], ctypes.c_char_p),
     "dg_abi_version": ([], _I32),
     "dg_kernel_launches": ([], _I64),
-    "dg_project": ([_P, _I64, _I64, _CAM, _I32, _OPT, _P, _P, _P, _P, _P, _P], _ST),
+    "dg_project": ([_P, _I64, _I64, _CAM, _P, _I32, _OPT, _P, _P, _P, _P, _P, _P], _ST),
     "dg_bin_workspace_size": ([_I64, _I32, _I64], _SZ),
     "dg_bin_count": ([_P, _P, _I64, _I32, _P, _SZ, _I64, _P, _P], _ST),
     "dg_bin_sort": ([_P, _P, _I64, _CAM, _I32, _I32, _P, _SZ, _I64, _P, _P, _P, _P], _ST),
     "dg_render_workspace_size": ([_CAM, _I32, _OPT], _SZ),
     "dg_render_fwd": ([_P, _P, _P, _CAM, _I32, _OPT, _P, _P, _P, _P, _P, _P, _SZ, _P], _ST),
     "dg_render_bwd": ([_P, _P, _P, _CAM, _I32, _OPT, _P, _P, _P, _I64, _P, _P, _SZ, _P], _ST),
-    "dg_project_bwd": ([_P, _I64, _I64, _CAM, _I32, _OPT, _P, _P, _P, _P, _P], _ST),
-    "dg_project_bwd_adam": ([_P, _I64, _I64, _CAM, _I32, _OPT, _P, _P, _P, _P, _P, _P, _P, ctypes.c_float,
+    "dg_project_bwd": ([_P, _I64, _I64, _CAM, _P, _I32, _OPT, _P, _P, _P, _P, _P], _ST),
+    "dg_project_bwd_adam": ([_P, _I64, _I64, _CAM, _P, _I32, _OPT, _P, _P, _P, _P, _P, _P, _P, ctypes.c_float,
                              ctypes.c_float, ctypes.c_float, _I64, _P], _ST),
     "dg_ssim_workspace_size": ([_P, _I32], _SZ),
     "dg_loss_l1_dssim": ([_P, _P, _P, _I32, ctypes.c_float, _P, _P, _P, _SZ, _P], _ST),
@@ -137,6 +137,8 @@ _SIGS = {
     "dg_loss_l1": ([_P, _P, _I64, _P, _P, _P, _SZ, _P], _ST),
     "dg_loss_l1_noalloc": ([_P, _P, _I64, _P, _P, _P], _ST),
     "dg_adam_step": ([_P, _P, _P, _P, _I64, _I64, _P, _F, _F, _F, _I64, _P], _ST),
+    "dg_adam_hparams_fill": ([_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I64, _P], _ST),
+    "dg_adam_step_dev": ([_P, _P, _P, _P, _I64, _I64, _P, _P, _P], _ST),
     "dg_spectrum_workspace_size": ([_I32, _I32], _SZ),
     "dg_spectrum_accumulate": ([_P, _I32, _I32, _P, _P, _SZ, _P], _ST),
     "dg_spectrum_finalize": ([_P, _I32, _I32, _I32, _P, _P, _P], _ST),
@@ -211,9 +213,11 @@ def dg_kernel_launches() -> int:
     return _lib.dg_kernel_launches()
 
 
-def dg_project(params, stride, P, cams, n_views, opts, feat, depth, radius, tiles, clamp, stream=None):
-    _check(_lib.dg_project(_a(params), stride, P, _c(cams), n_views, ctypes.byref(opts), _a(feat), _a(depth),
-                           _a(radius), _a(tiles), _a(clamp), _s(stream)))
+def dg_project(params, stride, P, cams, n_views, opts, feat, depth, radius, tiles, clamp, stream=None,
+               cams_dev=None):
+    """cams: host cameras; cams_dev: optional device copy (read when the kernel runs)."""
+    _check(_lib.dg_project(_a(params), stride, P, _c(cams), _a(cams_dev), n_views, ctypes.byref(opts), _a(feat),
+                           _a(depth), _a(radius), _a(tiles), _a(clamp), _s(stream)))
 
 
 def dg_bin_workspace_size(P, n_views, M_cap) -> int:
@@ -245,18 +249,17 @@ def dg_render_bwd(feat, gid, ranges, cams, n_views, opts, T_final, last, dL_dimg
                               _a(last), _a(dL_dimg), n_records, _a(grad2d), _a(ws), ws_bytes, _s(stream)))
 
 
-def dg_project_bwd(params, stride, P, cams, n_views, opts, radius, clamp, grad2d, grads, stream=None):
-    _check(_lib.dg_project_bwd(_a(params), stride, P, _c(cams), n_views, ctypes.byref(opts), _a(radius), _a(clamp),
-                               _a(grad2d), _a(grads), _s(stream)))
+def dg_project_bwd(params, stride, P, cams, n_views, opts, radius, clamp, grad2d, grads, stream=None, cams_dev=None):
+    _check(_lib.dg_project_bwd(_a(params), stride, P, _c(cams), _a(cams_dev), n_views, ctypes.byref(opts), _a(radius),
+                               _a(clamp), _a(grad2d), _a(grads), _s(stream)))
 
 
 def dg_project_bwd_adam(params, stride, P, cams, n_views, opts, radius, clamp, grad2d, grads, m, v, lr, beta1,
-                        beta2, eps, step, stream=None):
+                        beta2, eps, step, stream=None, cams_dev=None):
     lr_arr = (ctypes.c_float * NPARAM)(*[float(x) for x in lr])
-    _check(_lib.dg_project_bwd_adam(_a(params), stride, P, _c(cams), n_views, ctypes.byref(opts), _a(radius),
-                                    _a(clamp), _a(grad2d), _a(grads), _a(m), _a(v), ctypes.cast(lr_arr, ctypes.c_void_p), beta1,
-                                    beta2, eps, step,
-                                    _s(stream)))
+    _check(_lib.dg_project_bwd_adam(_a(params), stride, P, _c(cams), _a(cams_dev), n_views, ctypes.byref(opts),
+                                    _a(radius), _a(clamp), _a(grad2d), _a(grads), _a(m), _a(v),
+                                    ctypes.cast(lr_arr, ctypes.c_void_p), beta1, beta2, eps, step, _s(stream)))
 
 
 def dg_loss_workspace_size(n) -> int:
@@ -286,6 +289,24 @@ def dg_loss_l1_dssim(img, target, sizes, lam, dL_dimg, loss, ws, ws_bytes, strea
 def dg_loss_l1_noalloc(img, target, n, dL_dimg, loss, stream=None):
     """dg_loss_l1 without a workspace: for callers that cannot allocate device memory."""
     _check(_lib.dg_loss_l1_noalloc(_a(img), _a(target), n, _a(dL_dimg), _a(loss), _s(stream)))
+
+
+class AdamHparams(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float * NPARAM), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("bc1", ctypes.c_float), ("bc2_sqrt", ctypes.c_float), ("eps", ctypes.c_float)]
+
+
+def dg_adam_hparams_fill(lr, beta1, beta2, eps, step) -> AdamHparams:
+    lr_arr = (ctypes.c_float * NPARAM)(*[float(x) for x in lr])
+    out = AdamHparams()
+    _check(_lib.dg_adam_hparams_fill(ctypes.cast(lr_arr, ctypes.c_void_p), beta1, beta2, eps, step,
+                                     ctypes.byref(out)))
+    return out
+
+
+def dg_adam_step_dev(params, grads, m, v, stride, P, hp_dev, skip_if=None, stream=None):
+    _check(_lib.dg_adam_step_dev(_a(params), _a(grads), _a(m), _a(v), stride, P, _a(hp_dev), _a(skip_if),
+                                 _s(stream)))
 
 
 def dg_adam_step(params, grads, m, v, stride, P, lr, beta1, beta2, eps, step, stream=None):

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "../../include/dashgs.h"
@@ -25,7 +26,7 @@ struct Cam {
     int w, h;
 };
 
-inline Cam make_cam(const dg_camera& c)
+__host__ __device__ inline Cam make_cam(const dg_camera& c)
 {
     Cam k;
     for (int i = 0; i < 3; ++i) {
@@ -35,6 +36,13 @@ inline Cam make_cam(const dg_camera& c)
     k.fx = c.fx; k.fy = c.fy; k.cx = c.cx; k.cy = c.cy;
     k.w = c.width; k.h = c.height;
     return k;
+}
+
+// Camera centre in world coordinates, -R^T t, with explicit fused multiply-adds
+// so that host and device give the same bits.
+__host__ __device__ inline void cam_centre(const Cam& c, float out[3])
+{
+    for (int k = 0; k < 3; ++k) out[k] = -fmaf(c.r[k], c.t[0], fmaf(c.r[3 + k], c.t[1], c.r[6 + k] * c.t[2]));
 }
 
 __host__ __device__ inline long long floor_div(long long a, long long b)  // b > 0
@@ -61,19 +69,16 @@ __device__ inline Rect tile_rect(float u, float v, int r, int B, int TX, int TY)
     return q;
 }
 
-// Adam hyper-parameters of one step: per-row learning rate, betas, bias
-// corrections 1 - b1^t and sqrt(1 - b2^t), epsilon.
-struct AdamHp {
-    float lr[DG_NPARAM];
-    float b1, b2, bc1, bc2_sqrt, eps;
-};
+// Adam hyper-parameters of one step (the public dg_adam_hparams): per-row
+// learning rate, betas, bias corrections 1 - b1^t and sqrt(1 - b2^t), epsilon.
+using AdamHp = dg_adam_hparams;
 
 // One Adam update of a scalar parameter (shared by the standalone and the fused
 // kernels so that both give the same bits).
 __device__ __forceinline__ void adam_update(float& p, float& m, float& v, float g, float lr, const AdamHp& h)
 {
-    m = fmaf(h.b1, m, (1.f - h.b1) * g);
-    v = fmaf(h.b2, v, (1.f - h.b2) * (g * g));
+    m = fmaf(h.beta1, m, (1.f - h.beta1) * g);
+    v = fmaf(h.beta2, v, (1.f - h.beta2) * (g * g));
     p -= (lr / h.bc1) * m / (sqrtf(v) / h.bc2_sqrt + h.eps);
 }
 

@@ -87,11 +87,14 @@ __global__ void k_opacity_reset(float* __restrict__ prm, float* __restrict__ m, 
 // row start is 16-byte aligned, scalar otherwise).
 __global__ void __launch_bounds__(256)
 k_adam(float* __restrict__ prm, const float* __restrict__ grd, float* __restrict__ m,
-       float* __restrict__ v, long long stride, long long P, AdamHp hp)
+       float* __restrict__ v, long long stride, long long P, AdamHp hp_val, const AdamHp* __restrict__ hp_dev,
+       const int* __restrict__ skip_if)
 {
     const int row = blockIdx.y;
     const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     if (i0 >= P) return;
+    if (skip_if && *skip_if != 0) return;  // e.g. the step's pair list overflowed: no update
+    const AdamHp& hp = hp_dev ? *hp_dev : hp_val;
     const float lr = hp.lr[row];
     const long long o = (long long)row * stride + i0;
     const bool vec = ((o & 3) == 0) && (i0 + 3 < P) && ((((uintptr_t)prm) & 15u) == 0) &&
@@ -124,12 +127,34 @@ dg::AdamHp dg_adam_hp(const float* lr, float beta1, float beta2, float eps, int6
 {
     dg::AdamHp h;
     for (int i = 0; i < DG_NPARAM; ++i) h.lr[i] = lr[i];
-    h.b1 = beta1;
-    h.b2 = beta2;
+    h.beta1 = beta1;
+    h.beta2 = beta2;
     h.bc1 = (float)(1.0 - pow((double)beta1, (double)step));
     h.bc2_sqrt = (float)sqrt(1.0 - pow((double)beta2, (double)step));
     h.eps = eps;
     return h;
+}
+
+extern "C" dg_status dg_adam_hparams_fill(const float* lr, float beta1, float beta2, float eps, int64_t step,
+                                          dg_adam_hparams* out)
+{
+    if (!lr || !out || step < 1) { dg_set_error("lr/out null or step < 1"); return DG_ERR_ARG; }
+    *out = dg_adam_hp(lr, beta1, beta2, eps, step);
+    return DG_OK;
+}
+
+extern "C" dg_status dg_adam_step_dev(float* params, const float* grads, float* m, float* v, int64_t stride,
+                                      int64_t P, const dg_adam_hparams* hp_dev, const int32_t* skip_if,
+                                      dg_stream stream)
+{
+    if (P < 0 || stride < P) { dg_set_error("bad P/stride"); return DG_ERR_ARG; }
+    if (P == 0) return DG_OK;
+    if (!params || !grads || !m || !v || !hp_dev) { dg_set_error("null buffer"); return DG_ERR_ARG; }
+    const long long per = 256 * 4;
+    dim3 grid((unsigned)((P + per - 1) / per), DG_NPARAM);
+    dg::k_adam<<<grid, 256, 0, (cudaStream_t)stream>>>(params, grads, m, v, stride, P, dg::AdamHp{}, hp_dev, skip_if);
+    dg_note_launch();
+    return dg_check_launch("adam_dev");
 }
 
 extern "C" size_t dg_loss_workspace_size(int64_t n)
@@ -165,7 +190,7 @@ extern "C" dg_status dg_adam_step(float* params, const float* grads, float* m, f
     const dg::AdamHp hp = dg_adam_hp(lr, beta1, beta2, eps, step);
     const long long per = 256 * 4;
     dim3 grid((unsigned)((P + per - 1) / per), DG_NPARAM);
-    dg::k_adam<<<grid, 256, 0, (cudaStream_t)stream>>>(params, grads, m, v, stride, P, hp);
+    dg::k_adam<<<grid, 256, 0, (cudaStream_t)stream>>>(params, grads, m, v, stride, P, hp, nullptr, nullptr);
     dg_note_launch();
     return dg_check_launch("adam");
 }

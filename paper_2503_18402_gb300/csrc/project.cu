@@ -178,12 +178,35 @@ struct ViewSet {
     int TX[DG_MAX_VIEWS], TY[DG_MAX_VIEWS];
 };
 
+// The cameras a kernel uses: the by-value set built on the host, or, when the
+// caller passes a device copy of the cameras (read at execution time, e.g. on
+// every replay of a captured graph), the same set rebuilt from it in shared
+// memory (sizes and tile grids stay those of the host set).  Call with the
+// whole block; ends with a barrier when cdev is given.
+__device__ inline const ViewSet& block_views(const ViewSet& vs, const dg_camera* cdev, ViewSet* s_vs)
+{
+    if (!cdev) return vs;
+    for (int v = threadIdx.x; v < vs.n; v += blockDim.x) {
+        s_vs->cam[v] = make_cam(cdev[v]);
+        s_vs->cam[v].w = vs.cam[v].w;
+        s_vs->cam[v].h = vs.cam[v].h;
+        cam_centre(s_vs->cam[v], s_vs->campos[v]);
+        s_vs->TX[v] = vs.TX[v];
+        s_vs->TY[v] = vs.TY[v];
+    }
+    if (threadIdx.x == 0) s_vs->n = vs.n;
+    __syncthreads();
+    return *s_vs;
+}
+
 template <int NB>
 __global__ void __launch_bounds__(128)
-k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs, int B, float near_plane,
-              float eps2d, float4* __restrict__ feat, float* __restrict__ depth, int* __restrict__ radius,
-              int* __restrict__ tiles, uint8_t* __restrict__ clampm)
+k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs_host, const dg_camera* cdev, int B,
+              float near_plane, float eps2d, float4* __restrict__ feat, float* __restrict__ depth,
+              int* __restrict__ radius, int* __restrict__ tiles, uint8_t* __restrict__ clampm)
 {
+    __shared__ ViewSet s_vs;
+    const ViewSet& vs = block_views(vs_host, cdev, &s_vs);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
     G3 g;
@@ -252,10 +275,13 @@ k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs
 // (one column of every row), so the in-place update races with nothing.
 template <int NB, bool ADAM>
 __global__ void __launch_bounds__(128)
-k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs, float near_plane, float eps2d,
-              const int* __restrict__ radius, const uint8_t* __restrict__ clampm, const float4* __restrict__ grad2d,
-              float* __restrict__ grads, float* __restrict__ am, float* __restrict__ av, AdamHp hp)
+k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host, const dg_camera* cdev,
+              float near_plane, float eps2d, const int* __restrict__ radius, const uint8_t* __restrict__ clampm,
+              const float4* __restrict__ grad2d, float* __restrict__ grads, float* __restrict__ am,
+              float* __restrict__ av, AdamHp hp)
 {
+    __shared__ ViewSet s_vs;
+    const ViewSet& vs = block_views(vs_host, cdev, &s_vs);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
     auto put = [&](int row, float gval) {
@@ -444,17 +470,16 @@ static dg::ViewSet make_views(const dg_camera* cams, int n, int B)
     for (int v = 0; v < n; ++v) {
         const dg::Cam c = dg::make_cam(cams[v]);
         vs.cam[v] = c;
-        for (int k = 0; k < 3; ++k)
-            vs.campos[v][k] = -(c.r[k] * c.t[0] + c.r[3 + k] * c.t[1] + c.r[6 + k] * c.t[2]);
+        dg::cam_centre(c, vs.campos[v]);
         vs.TX[v] = (cams[v].width + B - 1) / B;
         vs.TY[v] = (cams[v].height + B - 1) / B;
     }
     return vs;
 }
 
-extern "C" dg_status dg_project(const float* params, int64_t stride, int64_t P, const dg_camera* cams, int32_t n_views,
-                                const dg_raster_opts* opts, float* feat, float* depth, int32_t* radius,
-                                int32_t* tiles, uint8_t* clamp, dg_stream stream)
+extern "C" dg_status dg_project(const float* params, int64_t stride, int64_t P, const dg_camera* cams,
+                                const dg_camera* cams_dev, int32_t n_views, const dg_raster_opts* opts, float* feat,
+                                float* depth, int32_t* radius, int32_t* tiles, uint8_t* clamp, dg_stream stream)
 {
     if (!dg_check_cameras(cams, n_views) || !check_opts(opts)) return DG_ERR_ARG;
     if (P < 0 || P > INT32_MAX || stride < P || (long long)P * n_views > (long long)UINT32_MAX) {
@@ -469,17 +494,18 @@ extern "C" dg_status dg_project(const float* params, int64_t stride, int64_t P, 
     const int blocks = (int)((P + threads - 1) / threads);
     cudaStream_t s = (cudaStream_t)stream;
     switch (opts->sh_degree) {
-    case 0: dg::k_project_fwd<1><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, opts->tile, opts->near_plane, opts->eps2d, (float4*)feat, depth, radius, tiles, clamp); break;
-    case 1: dg::k_project_fwd<4><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, opts->tile, opts->near_plane, opts->eps2d, (float4*)feat, depth, radius, tiles, clamp); break;
-    case 2: dg::k_project_fwd<9><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, opts->tile, opts->near_plane, opts->eps2d, (float4*)feat, depth, radius, tiles, clamp); break;
-    default: dg::k_project_fwd<16><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, opts->tile, opts->near_plane, opts->eps2d, (float4*)feat, depth, radius, tiles, clamp); break;
+    case 0: dg::k_project_fwd<1><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, (float4*)feat, depth, radius, tiles, clamp); break;
+    case 1: dg::k_project_fwd<4><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, (float4*)feat, depth, radius, tiles, clamp); break;
+    case 2: dg::k_project_fwd<9><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, (float4*)feat, depth, radius, tiles, clamp); break;
+    default: dg::k_project_fwd<16><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, (float4*)feat, depth, radius, tiles, clamp); break;
     }
     dg_note_launch();
     return dg_check_launch("project_fwd");
 }
 
 template <bool ADAM>
-static dg_status project_bwd(float* params, int64_t stride, int64_t P, const dg_camera* cams, int32_t n_views,
+static dg_status project_bwd(float* params, int64_t stride, int64_t P, const dg_camera* cams,
+                             const dg_camera* cams_dev, int32_t n_views,
                              const dg_raster_opts* opts, const int32_t* radius, const uint8_t* clamp,
                              const float* grad2d, float* grads, float* m, float* v, const dg::AdamHp& hp,
                              dg_stream stream)
@@ -502,31 +528,32 @@ static dg_status project_bwd(float* params, int64_t stride, int64_t P, const dg_
     const long long st = (long long)stride;
     const float4* g2 = (const float4*)grad2d;
     switch (opts->sh_degree) {
-    case 0: dg::k_project_bwd<1, ADAM><<<blocks, threads, 0, s>>>(params, st, (int)P, vs, opts->near_plane, opts->eps2d, radius, clamp, g2, grads, m, v, hp); break;
-    case 1: dg::k_project_bwd<4, ADAM><<<blocks, threads, 0, s>>>(params, st, (int)P, vs, opts->near_plane, opts->eps2d, radius, clamp, g2, grads, m, v, hp); break;
-    case 2: dg::k_project_bwd<9, ADAM><<<blocks, threads, 0, s>>>(params, st, (int)P, vs, opts->near_plane, opts->eps2d, radius, clamp, g2, grads, m, v, hp); break;
-    default: dg::k_project_bwd<16, ADAM><<<blocks, threads, 0, s>>>(params, st, (int)P, vs, opts->near_plane, opts->eps2d, radius, clamp, g2, grads, m, v, hp); break;
+    case 0: dg::k_project_bwd<1, ADAM><<<blocks, threads, 0, s>>>(params, st, (int)P, vs, cams_dev, opts->near_plane, opts->eps2d, radius, clamp, g2, grads, m, v, hp); break;
+    case 1: dg::k_project_bwd<4, ADAM><<<blocks, threads, 0, s>>>(params, st, (int)P, vs, cams_dev, opts->near_plane, opts->eps2d, radius, clamp, g2, grads, m, v, hp); break;
+    case 2: dg::k_project_bwd<9, ADAM><<<blocks, threads, 0, s>>>(params, st, (int)P, vs, cams_dev, opts->near_plane, opts->eps2d, radius, clamp, g2, grads, m, v, hp); break;
+    default: dg::k_project_bwd<16, ADAM><<<blocks, threads, 0, s>>>(params, st, (int)P, vs, cams_dev, opts->near_plane, opts->eps2d, radius, clamp, g2, grads, m, v, hp); break;
     }
     dg_note_launch();
     return dg_check_launch(ADAM ? "project_bwd_adam" : "project_bwd");
 }
 
 extern "C" dg_status dg_project_bwd(const float* params, int64_t stride, int64_t P, const dg_camera* cams,
-                                    int32_t n_views, const dg_raster_opts* opts, const int32_t* radius,
-                                    const uint8_t* clamp, const float* grad2d, float* grads, dg_stream stream)
+                                    const dg_camera* cams_dev, int32_t n_views, const dg_raster_opts* opts,
+                                    const int32_t* radius, const uint8_t* clamp, const float* grad2d, float* grads,
+                                    dg_stream stream)
 {
     // the non-Adam instantiation never writes params
-    return project_bwd<false>(const_cast<float*>(params), stride, P, cams, n_views, opts, radius, clamp, grad2d,
-                              grads, nullptr, nullptr, dg::AdamHp{}, stream);
+    return project_bwd<false>(const_cast<float*>(params), stride, P, cams, cams_dev, n_views, opts, radius, clamp,
+                              grad2d, grads, nullptr, nullptr, dg::AdamHp{}, stream);
 }
 
 extern "C" dg_status dg_project_bwd_adam(float* params, int64_t stride, int64_t P, const dg_camera* cams,
-                                         int32_t n_views, const dg_raster_opts* opts, const int32_t* radius,
-                                         const uint8_t* clamp, const float* grad2d, float* grads, float* m, float* v,
-                                         const float* lr, float beta1, float beta2, float eps, int64_t step,
-                                         dg_stream stream)
+                                         const dg_camera* cams_dev, int32_t n_views, const dg_raster_opts* opts,
+                                         const int32_t* radius, const uint8_t* clamp, const float* grad2d,
+                                         float* grads, float* m, float* v, const float* lr, float beta1, float beta2,
+                                         float eps, int64_t step, dg_stream stream)
 {
     if (step < 1 || !lr) { dg_set_error("step must be >= 1 and lr given"); return DG_ERR_ARG; }
-    return project_bwd<true>(params, stride, P, cams, n_views, opts, radius, clamp, grad2d, grads, m, v,
+    return project_bwd<true>(params, stride, P, cams, cams_dev, n_views, opts, radius, clamp, grad2d, grads, m, v,
                              dg_adam_hp(lr, beta1, beta2, eps, step), stream);
 }

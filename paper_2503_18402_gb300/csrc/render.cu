@@ -118,6 +118,15 @@ constexpr float kLog2e = 1.4426950408889634f;
 // exponential, identically in the forward and the backward
 constexpr float kLog2AlphaMin = -7.994353436858858f;
 
+// Backward: a warp whose contributing lanes number at most this many adds their
+// partial gradients with per-lane vector atomics instead of reducing first
+// (0: always reduce).  A launch-shape constant: results differ only in the
+// order of the float additions.
+#ifndef DG_BWD_DIRECT_LANES
+#define DG_BWD_DIRECT_LANES 0
+#endif
+constexpr int kBwdDirectLanes = DG_BWD_DIRECT_LANES;
+
 // Stable block-wide compaction index of `keep`; *total = number kept.  Ends with a barrier.
 template <int NT>
 __device__ inline int compact_index(bool keep, int* s_w, int* total)
@@ -681,7 +690,19 @@ k_render_bwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
                     }
                 }
             }
-            if (!__any_sync(0xffffffffu, any)) continue;
+            const unsigned anym = __ballot_sync(0xffffffffu, any);
+            if (!anym) continue;
+            if (kBwdDirectLanes > 0 && __popc(anym) <= kBwdDirectLanes) {
+                // few contributing lanes: each adds its own partial sums (three
+                // vector atomics) instead of the 12-shuffle warp reduction
+                if (any) {
+                    float4* gp = grad2d + 3 * (size_t)s_g[kk];
+                    atomicAdd(gp, make_float4(du, dv, dA, dB));
+                    atomicAdd(gp + 1, make_float4(dC, dop, dr, dgc));
+                    atomicAdd((float*)(gp + 2), db);
+                }
+                continue;
+            }
             const float vals[9] = {du, dv, dA, dB, dC, dop, dr, dgc, db};
             int idx;
             const float tot = warp_sum9(vals, lane, &idx);

@@ -109,6 +109,47 @@ class Rasterizer:
         if self.rws is None or self.rws.numel() < need:
             self.rws = torch.empty(need, dtype=torch.uint8, device=self.device)
 
+    # ------------------------------------------------------------ fixed-capacity passes
+    def prepare(self, P: int, cams, M_cap: int) -> None:
+        """Allocates every buffer a batch of these cameras needs with room for
+        M_cap pairs, so that forward_fixed/backward_render allocate nothing
+        (as required inside a CUDA graph capture)."""
+        cams = [cams] if isinstance(cams, capi.Camera) else list(cams)
+        V = len(cams)
+        carr = capi.cameras(cams)
+        B = self.opts.tile
+        n_tiles = sum(((c.width + B - 1) // B) * ((c.height + B - 1) // B) for c in cams)
+        npix = sum(c.width * c.height for c in cams)
+        self._ensure_records(V * P)
+        self._ensure_tiles(n_tiles)
+        self._ensure_ws(P, V, max(int(M_cap), self.M_cap, 1))
+        self._ensure_rws(carr, V)
+        d = self.device
+        self.fixed = dict(img=torch.empty(3 * npix, dtype=torch.float32, device=d),
+                          T=torch.empty(npix, dtype=torch.float32, device=d),
+                          last=torch.empty(npix, dtype=torch.int32, device=d))
+
+    def forward_fixed(self, params: torch.Tensor, P: int, cams, stream=None, cams_dev=None) -> Frame:
+        """forward() without the host read of the pair count: bins with the
+        capacity set by prepare() (a larger count sets the device status word
+        self.status to DG_ERR_CAPACITY and renders empty tiles); no allocation,
+        no synchronisation.  cams_dev: optional device copy of the cameras."""
+        cams = [cams] if isinstance(cams, capi.Camera) else list(cams)
+        V = len(cams)
+        carr = capi.cameras(cams)
+        stream = stream or torch.cuda.current_stream(self.device)
+        B = self.opts.tile
+        capi.dg_project(params, params.stride(0), P, carr, V, self.opts, self.feat, self.depth, self.radius,
+                        self.tiles, self.clamp, stream, cams_dev=cams_dev)
+        capi.dg_bin_count(self.depth, self.tiles, P, V, self.ws, self.ws.numel(), self.M_cap, self.M_dev, stream)
+        capi.dg_bin_sort(self.feat, self.radius, P, carr, V, B, self.ws, self.ws.numel(), self.M_cap, self.gid,
+                         self.ranges, self.status, stream)
+        f = self.fixed
+        capi.dg_render_fwd(self.feat, self.gid, self.ranges, carr, V, self.opts_fwd, f["img"], f["T"], f["last"],
+                           None, None, self.rws, self.rws.numel(), stream)
+        return Frame(P=P, cams=cams, img=f["img"], T=f["T"], last=f["last"], M=-1, flat_img=f["img"],
+                     flat_T=f["T"], flat_last=f["last"])
+
     # ------------------------------------------------------------ passes
     def forward(self, params: torch.Tensor, P: int, cams, stream=None, examined: bool = False) -> Frame:
         """Project, bin, sort and composite P Gaussians of the planar

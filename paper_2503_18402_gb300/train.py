@@ -31,6 +31,7 @@ import torch
 
 from . import capi
 from .autotune import RenderTuner, Shape
+from .graphstep import StepGraph
 from .raster import Rasterizer, make_camera
 from .schedule import spectrum_table
 
@@ -39,6 +40,11 @@ from .schedule import spectrum_table
 class TrainConfig:
     iters: int = 30000
     scheduled: bool = True
+    # ablations of the scheduled arm (both on = the full method): resolution
+    # schedule (render at floor(r(k)), position LR held until full resolution)
+    # and primitive schedule (Eq. 4/5 budget, densification until full resolution)
+    reso_sched: bool = True
+    prim_sched: bool = True
     densify_from: int = 500
     densify_until: int = 15000
     densify_every: int = 100
@@ -70,6 +76,10 @@ class TrainConfig:
     ssim_lambda: float = 0.2
     # render launch shape: chosen per (image size, P) bucket by timing, or fixed
     autotune: bool = True
+    # views rendered per step (one multi-view launch per pass) and capture of
+    # the whole step in a CUDA graph (replayed with new cameras / LR / targets)
+    views_per_step: int = 1
+    cuda_graph: bool = False
     # projection adjoint fused with the Adam update (no stored gradient); off:
     # the fused kernel's register footprint (one thread per Gaussian holding all
     # 59 gradients) leaves too few warps resident to stream params, m and v
@@ -118,6 +128,12 @@ class Trainer:
         self.history = []
         self.init_schedule_s = 0.0
         self.densify_until = cfg.densify_until
+        self.graphs = {}
+        self.graph_P = -1
+        self.M_hint = {}
+        self.pending = None  # (StepGraph) whose status is read one step later
+        self.skipped_steps = 0
+        self.graph_captures = 0
 
     # ---------------------------------------------------------------- schedule
     def init_schedule(self):
@@ -128,14 +144,14 @@ class Trainer:
                               P_cap=float(cfg.P_cap), lr_pos_init=cfg.lr_pos_init * cfg.extent,
                               lr_pos_final=cfg.lr_pos_final * cfg.extent)
         self.sched = capi.dg_schedule_init(sat, self.H, self.W, p)
-        if cfg.densify_until_full:
+        if cfg.densify_until_full and cfg.prim_sched:
             self.densify_until = max(cfg.densify_until, int(self.sched.k_full))
         torch.cuda.synchronize()
         self.init_schedule_s = time.perf_counter() - t0
 
     def _plan(self, k):
         cfg = self.cfg
-        if self.sched is not None:
+        if self.sched is not None and cfg.reso_sched:
             o = capi.dg_schedule_step(self.sched, k)
             return o.r_mod, o.height, o.width, o.lr_pos
         t = min(1.0, k / cfg.iters)
@@ -165,8 +181,97 @@ class Trainer:
         return int(self.order.pop())
 
     # ---------------------------------------------------------------- step
+    def _lr(self, lr_pos):
+        cfg = self.cfg
+        return [lr_pos] * 3 + [cfg.lr_scale] * 3 + [cfg.lr_rot] * 4 + [cfg.lr_opacity] + [cfg.lr_dc] * 3 + \
+            [cfg.lr_rest] * 45
+
+    def _step_batched(self, k):
+        """V views per step through the multi-view calls; with cuda_graph the
+        whole step is one graph replay."""
+        cfg = self.cfg
+        b = self.buf[self.cur]
+        P = self.P
+        V = cfg.views_per_step
+        r, h, w, lr_pos = self._plan(k)
+        js = [self._next_view() for _ in range(V)]
+        cams = [self._camera(j, h, w) for j in js]
+        targets = [self._target(j, r, h, w) for j in js]
+        lr = self._lr(lr_pos)
+        stats_on = k < self.densify_until
+        if not cfg.cuda_graph:
+            shape, rz, key = self.tuner.pick(V * h * w, P)
+            e0 = self.tuner.start(self.stream)
+            params = b["p"][:, :P]
+            fr = rz.forward(params, P, cams, self.stream)
+            tgt = torch.cat([t.reshape(-1) for t in targets])
+            n = tgt.numel()
+            capi.dg_loss_l1_dssim(fr.flat_img, tgt, [(w, h)] * V, cfg.ssim_lambda, self.dL_b(n), self.loss_b(V),
+                                  self.sws_b([(w, h)] * V), self.sws_batch.numel(), self.stream)
+            rz.backward_render(fr, self._dLb[:n], self.stream)
+            self.tuner.stop(key, shape, e0, self.stream)
+            if stats_on:
+                capi.dg_densify_stats(rz.grad2d, rz.radius, P, cams, V, self.acc, self.den, self.maxr, self.stream)
+            capi.dg_project_bwd(params, self.cap, P, cams, V, rz.opts, rz.radius, rz.clamp, rz.grad2d,
+                                self.grads[:, :P], self.stream)
+            capi.dg_adam_step(b["p"], self.grads, b["m"], b["v"], self.cap, P, lr, 0.9, 0.999, 1e-15, k + 1,
+                              self.stream)
+            return r, fr.M
+        # graph path: one graph per (P, size, stats window, buffer set); read the
+        # previous step's status one step late (no wait inside the loop)
+        if self.pending is not None:
+            g_prev = self.pending
+            status, M = g_prev.result()
+            sz = g_prev.sizes[0]
+            self.M_hint[sz] = max(self.M_hint.get(sz, 0), M)
+            if status != 0:  # pair capacity exceeded: that step made no update
+                self.skipped_steps += 1
+                self.graphs.pop(g_prev.key, None)
+        if P != self.graph_P:
+            self.graphs.clear()
+            self.graph_P = P
+        hp = capi.dg_adam_hparams_fill(lr, 0.9, 0.999, 1e-15, k + 1)
+        key = (P, h, w, V, stats_on, self.cur)
+        g = self.graphs.get(key)
+        if g is None:
+            hint = self.M_hint.get((w, h))
+            if hint is None:  # first batch at this size: count its pairs once
+                rz0 = self.tuner.rasterizer(Shape(8, 1, 1, 0))
+                fr0 = rz0.forward(b["p"][:, :P], P, cams, self.stream)
+                hint = fr0.M
+            M_cap = int(hint * 1.5) + 4096
+            g = StepGraph(self.dev, capi.raster_opts(tile=8), 1, 1, b["p"], b["m"], b["v"], self.grads, self.cap, P,
+                          cams, M_cap, cfg.ssim_lambda, (self.acc, self.den, self.maxr) if stats_on else None)
+            g.key = key
+            g.capture(cams, hp, targets)
+            self.graphs[key] = g
+            self.graph_captures += 1
+        else:
+            g.replay(cams, hp, targets)
+        self.pending = g
+        self.loss = g.loss
+        return r, -1
+
+    def dL_b(self, n):
+        if getattr(self, "_dLb", None) is None or self._dLb.numel() < n:
+            self._dLb = torch.empty(n, dtype=torch.float32, device=self.dev)
+        return self._dLb
+
+    def loss_b(self, V):
+        if self.loss.numel() < V + 1:
+            self.loss = torch.zeros(V + 1, dtype=torch.float32, device=self.dev)
+        return self.loss
+
+    def sws_b(self, sizes):
+        need = capi.dg_ssim_workspace_size(sizes)
+        if getattr(self, "sws_batch", None) is None or self.sws_batch.numel() < need:
+            self.sws_batch = torch.empty(need, dtype=torch.uint8, device=self.dev)
+        return self.sws_batch
+
     def step(self, k):
         cfg = self.cfg
+        if cfg.views_per_step > 1 or cfg.cuda_graph:
+            return self._step_batched(k)
         b = self.buf[self.cur]
         P = self.P
         r, h, w, lr_pos = self._plan(k)
@@ -218,7 +323,7 @@ class Trainer:
         capi.dg_densify_mark(b["p"], self.cap, P, self.acc, self.den, self.maxr, opts, self.dws, self.dws.numel(),
                              self.counts, self.stream)
         n_keep, n_cand = (int(x) for x in self.counts.cpu())
-        if self.sched is not None:
+        if self.sched is not None and cfg.prim_sched:
             o = capi.dg_schedule_densify(self.sched, k, n_cand)
             budget = max(0, int(o.P_target) - n_keep)
         else:
@@ -260,9 +365,14 @@ class Trainer:
                 print(json.dumps(dict(iter=k + 1, P=self.P, r=r, loss=float(self.loss[0].item()),
                                       s=round(time.perf_counter() - t0, 2))), flush=True)
         torch.cuda.synchronize()
+        if self.pending is not None:
+            status, _ = self.pending.result()
+            self.skipped_steps += int(status != 0)
         return dict(seconds=time.perf_counter() - t0, schedule_init_s=self.init_schedule_s, P_final=self.P,
                     iters_per_factor={str(k): v for k, v in sorted(res_hist.items())},
-                    render_shapes=self.tuner.summary())
+                    render_shapes=self.tuner.summary(), views_per_step=cfg.views_per_step,
+                    cuda_graph=cfg.cuda_graph, graph_captures=self.graph_captures,
+                    skipped_steps=self.skipped_steps)
 
 
 def make_dataset(n_gt, n_views, W, H, device, seed=1001):
@@ -284,7 +394,11 @@ def make_dataset(n_gt, n_views, W, H, device, seed=1001):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("--arm", choices=["plain", "scheduled", "both"], default="both")
+    ap.add_argument("--arm", choices=["plain", "scheduled", "both", "reso", "prim", "all"], default="both",
+                    help="both = plain + scheduled; reso / prim = the scheduled arm with only the resolution / "
+                         "only the primitive schedule; all = the four")
+    ap.add_argument("--a", type=float, default=4.0, help="r_m from X(r_m) = X(1)/a (Sec. 4.2)")
+    ap.add_argument("--gamma", type=float, default=0.98, help="Eq. 5 momentum")
     ap.add_argument("--iters", type=int, default=30000)
     ap.add_argument("--n-gt", type=int, default=2_000_000)
     ap.add_argument("--n-init", type=int, default=100_000)
@@ -295,16 +409,20 @@ def main(argv=None):
     ap.add_argument("--log-every", type=int, default=0)
     ap.add_argument("--ssim-lambda", type=float, default=0.2)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--views-per-step", type=int, default=1)
+    ap.add_argument("--cuda-graph", action="store_true", help="capture each step in a CUDA graph")
     args = ap.parse_args(argv)
     from . import synth
     dev = torch.device("cuda")
     gt, cams, imgs, train, test = make_dataset(args.n_gt, args.views, args.width, args.height, dev)
     init = synth.perturb(gt, 3001, n_keep=args.n_init)
-    arms = ["plain", "scheduled"] if args.arm == "both" else [args.arm]
+    arms = {"both": ["plain", "scheduled"], "all": ["plain", "scheduled", "reso", "prim"]}.get(args.arm, [args.arm])
     results = {}
     for arm in arms:
-        cfg = TrainConfig(iters=args.iters, scheduled=(arm == "scheduled"), P_cap=args.p_cap,
-                          ssim_lambda=args.ssim_lambda, autotune=not args.no_autotune)
+        cfg = TrainConfig(iters=args.iters, scheduled=(arm != "plain"), P_cap=args.p_cap,
+                          reso_sched=arm in ("scheduled", "reso"), prim_sched=arm in ("scheduled", "prim"),
+                          a=args.a, gamma=args.gamma, ssim_lambda=args.ssim_lambda, autotune=not args.no_autotune,
+                          views_per_step=args.views_per_step, cuda_graph=args.cuda_graph)
         if args.iters < 30000:  # compress the backbone's iteration windows proportionally
             s = args.iters / 30000
             cfg.densify_from = max(1, int(500 * s)); cfg.densify_until = int(15000 * s)
