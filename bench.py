@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-gauss", type=int, default=N_GAUSS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--record", choices=["fp32", "mixed"], default="fp32",
+                    help="render-side record storage (mixed: float16 conic/opacity, bfloat16 colour)")
     ap.add_argument("--fused-adam", action="store_true",
                     help="projection adjoint fused with Adam (default: two kernels)")
     ap.add_argument("--cpu-frac", type=float, default=0.125,
@@ -55,12 +57,14 @@ def parse():
 
 
 def config(args, n_gauss, shape=None):
-    return {"workload": f"textured-{n_gauss // 1000}k-gaussians-{W_FULL}x{H_FULL}-1view-fp32",
+    prec = "mixed" if args.record == "mixed" else "fp32"
+    return {"workload": f"textured-{n_gauss // 1000}k-gaussians-{W_FULL}x{H_FULL}-1view-{prec}",
             "n_gaussians": n_gauss, "width": W_FULL, "height": H_FULL, "views_per_step": 1,
             "tile": shape.tile if shape else 16, "render_shape": shape.label() if shape else None,
             "sh_degree": 3, "loss": "0.8 L1 + 0.2 D-SSIM",
             "step": "project+bin+render_fwd+loss+render_bwd+project_bwd+adam",
             "adjoint_adam": "fused" if args.fused_adam else "two kernels",
+            "render_records": "mixed fp16/bf16" if args.record == "mixed" else "fp32",
             "l2": "working set 1.9 GB > L2 (no flush)", "parallelism": f"replicas{args.gpus}"}
 
 
@@ -135,8 +139,8 @@ def run_ours(args):
     P = gt.shape[0]
     gcams = [make_camera(np.asarray(v["viewmat"], np.float32).reshape(-1), v["intr"], v["width"], v["height"])
              for v in views]
-    opts = capi.raster_opts(tile=16, sh_degree=3)
-    rz = Rasterizer(dev, opts)
+    opts = capi.raster_opts(tile=16, sh_degree=3, record=1 if args.record == "mixed" else 0)
+    rz = Rasterizer(dev, capi.raster_opts(tile=16, sh_degree=3))
     gt_t = torch.from_numpy(np.ascontiguousarray(gt.T)).to(dev)
     targets = []
     for c in gcams:

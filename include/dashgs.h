@@ -90,7 +90,10 @@ typedef struct dg_camera {
  * CTAs)), > 0 = always split with that L (raised where the workspace needs
  * it), < 0 = never split.
  * pixels_per_thread and split_len change the launch shape only, not the
- * result beyond float rounding order. */
+ * result beyond float rounding order.  record: format of the records the
+ * render calls read: 0 = the float32 records of dg_project, 1 = the
+ * mixed-precision records of dg_pack_records (float16 conic and opacity,
+ * bfloat16 colour; transmittance, colour sums and gradients stay float32). */
 typedef struct dg_raster_opts {
     int32_t tile;
     int32_t sh_degree;
@@ -99,6 +102,7 @@ typedef struct dg_raster_opts {
     float bg[3];
     int32_t pixels_per_thread;
     int32_t split_len;
+    int32_t record;
 } dg_raster_opts;
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
@@ -172,6 +176,16 @@ DG_API dg_status dg_bin_count(const float* depth, const int32_t* tiles, int64_t 
 DG_API dg_status dg_bin_sort(const float* feat, const int32_t* radius, int64_t P, const dg_camera* cams,
                       int32_t n_views, int32_t tile, void* ws, size_t ws_bytes, int64_t M_cap, uint32_t* gid,
                       uint32_t* ranges, int32_t* status, dg_stream stream);
+
+/* Mixed-precision records for the render calls (opts->record = 1): each
+ * float32 record of dg_project becomes 24 bytes, u and v float32 (pixel
+ * positions need the full mantissa at 1600 px), conic A, B, C and opacity
+ * float16 (round to nearest), colour r, g, b bfloat16 (round to nearest),
+ * two bytes of zero padding.  packed: n_records * 24 bytes, 8-byte aligned.
+ * Binning keeps reading the float32 records, so the pair lists are those of
+ * the float32 path. */
+#define DG_PACKED_RECORD_BYTES 24
+DG_API dg_status dg_pack_records(const float* feat, int64_t n_records, void* packed, dg_stream stream);
 
 /* ---------------------------------------------------------------------- */
 /* Render workspace for these cameras and options: work counters of the

@@ -24,7 +24,7 @@ DG_OK, DG_ERR_ARG, DG_ERR_CAPACITY, DG_ERR_TIMEOUT, DG_ERR_CUDA = 0, -1, -2, -3,
 
 MAX_VIEWS = 16
 EXPORTS = ("dg_last_error", "dg_abi_version", "dg_kernel_launches", "dg_project", "dg_bin_workspace_size", "dg_bin_count",
-           "dg_bin_sort", "dg_render_workspace_size", "dg_render_fwd", "dg_render_bwd", "dg_project_bwd", "dg_project_bwd_adam",
+           "dg_bin_sort", "dg_render_workspace_size", "dg_render_fwd", "dg_render_bwd", "dg_pack_records", "dg_project_bwd", "dg_project_bwd_adam",
            "dg_loss_workspace_size", "dg_ssim_workspace_size", "dg_loss_l1_dssim",
            "dg_loss_l1", "dg_loss_l1_noalloc", "dg_adam_step", "dg_adam_hparams_fill", "dg_adam_step_dev", "dg_spectrum_workspace_size",
            "dg_spectrum_accumulate", "dg_spectrum_finalize", "dg_downsample_area", "dg_schedule_init",
@@ -48,7 +48,7 @@ class Camera(ctypes.Structure):
 class RasterOpts(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("near_plane", ctypes.c_float),
                 ("eps2d", ctypes.c_float), ("bg", ctypes.c_float * 3), ("pixels_per_thread", ctypes.c_int32),
-                ("split_len", ctypes.c_int32)]
+                ("split_len", ctypes.c_int32), ("record", ctypes.c_int32)]
 
 
 SCHED_MAX_LEVELS = 64
@@ -99,12 +99,13 @@ def camera(viewmat, fx, fy, cx, cy, width, height) -> Camera:
 
 
 def raster_opts(tile=16, sh_degree=3, near_plane=0.2, eps2d=0.3, bg=(0.0, 0.0, 0.0),
-                pixels_per_thread=0, split_len=0) -> RasterOpts:
+                pixels_per_thread=0, split_len=0, record=0) -> RasterOpts:
     o = RasterOpts()
     o.tile, o.sh_degree, o.near_plane, o.eps2d = int(tile), int(sh_degree), float(near_plane), float(eps2d)
     o.bg[:] = [float(b) for b in bg]
     o.pixels_per_thread = int(pixels_per_thread)
     o.split_len = int(split_len)
+    o.record = int(record)
     return o
 
 
@@ -126,6 +127,7 @@ _SIGS = {
     "dg_bin_count": ([_P, _P, _I64, _I32, _P, _SZ, _I64, _P, _P], _ST),
     "dg_bin_sort": ([_P, _P, _I64, _CAM, _I32, _I32, _P, _SZ, _I64, _P, _P, _P, _P], _ST),
     "dg_render_workspace_size": ([_CAM, _I32, _OPT], _SZ),
+    "dg_pack_records": ([_P, _I64, _P, _P], _ST),
     "dg_render_fwd": ([_P, _P, _P, _CAM, _I32, _OPT, _P, _P, _P, _P, _P, _P, _SZ, _P], _ST),
     "dg_render_bwd": ([_P, _P, _P, _CAM, _I32, _OPT, _P, _P, _P, _I64, _P, _P, _SZ, _P], _ST),
     "dg_project_bwd": ([_P, _I64, _I64, _CAM, _P, _I32, _OPT, _P, _P, _P, _P, _P], _ST),
@@ -235,6 +237,13 @@ def dg_bin_sort(feat, radius, P, cams, n_views, tile, ws, ws_bytes, M_cap, gid, 
 
 def dg_render_workspace_size(cams, n_views, opts) -> int:
     return _lib.dg_render_workspace_size(_c(cams), n_views, ctypes.byref(opts))
+
+
+PACKED_RECORD_BYTES = 24
+
+
+def dg_pack_records(feat, n_records, packed, stream=None):
+    _check(_lib.dg_pack_records(_a(feat), n_records, _a(packed), _s(stream)))
 
 
 def dg_render_fwd(feat, gid, ranges, cams, n_views, opts, img, T_final, last, examined, blended, ws, ws_bytes,

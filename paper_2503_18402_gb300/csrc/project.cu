@@ -273,8 +273,11 @@ k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs
 // update of that row (params, m, v), so the fused form never stores or reloads
 // the gradient and reads the parameters once.  Each thread owns one Gaussian
 // (one column of every row), so the in-place update races with nothing.
-template <int NB, bool ADAM>
-__global__ void __launch_bounds__(128)
+// At most 128 registers (four 128-thread CTAs per SM): the adjoint streams
+// 0.5-1.5 kB per Gaussian, and the extra resident warps hide more memory
+// latency than the few spilled values cost.
+template <int NB, bool ADAM, bool SINGLE>
+__global__ void __launch_bounds__(128, 4)
 k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host, const dg_camera* cdev,
               float near_plane, float eps2d, const int* __restrict__ radius, const uint8_t* __restrict__ clampm,
               const float4* __restrict__ grad2d, float* __restrict__ grads, float* __restrict__ am,
@@ -300,9 +303,12 @@ k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host,
     float dp[3] = {0.f, 0.f, 0.f};
     float dsg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma (xx xy xz yy yz zz), off-diagonals counted once
     float dop = 0.f;
-    float dsh[NB][3];
+    // SH-coefficient gradients: summed over the views in registers, or, with a
+    // single view (SINGLE), emitted row by row as they are formed (no 48-float
+    // accumulator held across the kernel)
+    float dsh[SINGLE ? 1 : NB][3];
 #pragma unroll
-    for (int k = 0; k < NB; ++k) dsh[k][0] = dsh[k][1] = dsh[k][2] = 0.f;
+    for (int k = 0; k < (SINGLE ? 1 : NB); ++k) dsh[k][0] = dsh[k][1] = dsh[k][2] = 0.f;
     bool any = false;
     for (int v = 0; v < vs.n; ++v) {
         const size_t r = (size_t)v * P + i;
@@ -330,11 +336,12 @@ k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host,
             for (int k = 0; k < NB; ++k)
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
-                    dsh[k][ch] += Y[k] * dcol[ch];
                     const float cw = dcol[ch] * prm[(11 + 3 * k + ch) * stride + i];
                     gd[0] += cw * D[k][0];
                     gd[1] += cw * D[k][1];
                     gd[2] += cw * D[k][2];
+                    if (SINGLE) put(11 + 3 * k + ch, Y[k] * dcol[ch]);  // after the coefficient was read
+                    else dsh[SINGLE ? 0 : k][ch] += Y[k] * dcol[ch];
                 }
             const float dd = d0 * gd[0] + d1 * gd[1] + d2 * gd[2];
             dp[0] += (gd[0] - d0 * dd) * linv;
@@ -412,9 +419,9 @@ k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host,
         put(10, dop * o * (1.f - o));
     }
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
+    for (int k = SINGLE ? NB : 0; k < 16; ++k)
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) put(11 + 3 * k + ch, k < NB ? dsh[k][ch] : 0.f);
+        for (int ch = 0; ch < 3; ++ch) put(11 + 3 * k + ch, k < NB ? dsh[SINGLE ? 0 : k][ch] : 0.f);
     // Sigma = M M^T:  dM = 2 dSigma M;  M = Rq diag(s)
     const float ds[9] = {dsg[0], dsg[1], dsg[2], dsg[1], dsg[3], dsg[4], dsg[2], dsg[4], dsg[5]};
     float dR[9];
@@ -503,6 +510,21 @@ extern "C" dg_status dg_project(const float* params, int64_t stride, int64_t P, 
     return dg_check_launch("project_fwd");
 }
 
+template <bool ADAM, bool SINGLE>
+static void launch_project_bwd(int nb, int blocks, int threads, cudaStream_t s, float* params, long long st, int P,
+                               const dg::ViewSet& vs, const dg_camera* cams_dev, const dg_raster_opts* opts,
+                               const int32_t* radius, const uint8_t* clamp, const float4* g2, float* grads, float* m,
+                               float* v, const dg::AdamHp& hp)
+{
+    const float np = opts->near_plane, e2 = opts->eps2d;
+    switch (nb) {
+    case 1: dg::k_project_bwd<1, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, radius, clamp, g2, grads, m, v, hp); break;
+    case 4: dg::k_project_bwd<4, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, radius, clamp, g2, grads, m, v, hp); break;
+    case 9: dg::k_project_bwd<9, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, radius, clamp, g2, grads, m, v, hp); break;
+    default: dg::k_project_bwd<16, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, radius, clamp, g2, grads, m, v, hp); break;
+    }
+}
+
 template <bool ADAM>
 static dg_status project_bwd(float* params, int64_t stride, int64_t P, const dg_camera* cams,
                              const dg_camera* cams_dev, int32_t n_views,
@@ -527,12 +549,9 @@ static dg_status project_bwd(float* params, int64_t stride, int64_t P, const dg_
     cudaStream_t s = (cudaStream_t)stream;
     const long long st = (long long)stride;
     const float4* g2 = (const float4*)grad2d;
-    switch (opts->sh_degree) {
-    case 0: dg::k_project_bwd<1, ADAM><<<blocks, threads, 0, s>>>(params, st, (int)P, vs, cams_dev, opts->near_plane, opts->eps2d, radius, clamp, g2, grads, m, v, hp); break;
-    case 1: dg::k_project_bwd<4, ADAM><<<blocks, threads, 0, s>>>(params, st, (int)P, vs, cams_dev, opts->near_plane, opts->eps2d, radius, clamp, g2, grads, m, v, hp); break;
-    case 2: dg::k_project_bwd<9, ADAM><<<blocks, threads, 0, s>>>(params, st, (int)P, vs, cams_dev, opts->near_plane, opts->eps2d, radius, clamp, g2, grads, m, v, hp); break;
-    default: dg::k_project_bwd<16, ADAM><<<blocks, threads, 0, s>>>(params, st, (int)P, vs, cams_dev, opts->near_plane, opts->eps2d, radius, clamp, g2, grads, m, v, hp); break;
-    }
+    const int nb = opts->sh_degree == 0 ? 1 : opts->sh_degree == 1 ? 4 : opts->sh_degree == 2 ? 9 : 16;
+    if (n_views == 1) launch_project_bwd<ADAM, true>(nb, blocks, threads, s, params, st, (int)P, vs, cams_dev, opts, radius, clamp, g2, grads, m, v, hp);
+    else launch_project_bwd<ADAM, false>(nb, blocks, threads, s, params, st, (int)P, vs, cams_dev, opts, radius, clamp, g2, grads, m, v, hp);
     dg_note_launch();
     return dg_check_launch(ADAM ? "project_bwd_adam" : "project_bwd");
 }

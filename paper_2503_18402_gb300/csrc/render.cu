@@ -50,6 +50,10 @@
 // skip the entry, so it is dropped from the batch (stable compaction; the
 // original list position is kept for `last`).  Results are unchanged.
 #include <climits>
+#include <string.h>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 #include "radix.cuh"
@@ -146,6 +150,34 @@ __device__ inline int compact_index(bool keep, int* s_w, int* total)
     *total = tot;
     __syncthreads();
     return pre + __popc(bal & ((1u << lane) - 1u));
+}
+
+// One projected record as (u, v, A, B), (C, o, r, g), b.  REC 0: the FP32
+// record of dg_project (three float4).  REC 1: the mixed-precision record of
+// dg_pack_records (24 bytes: u, v float32 | A, B float16 | C, o float16 |
+// r, g bfloat16 | b bfloat16, pad), widened to float32 here; all arithmetic
+// after the load is float32.
+template <int REC>
+__device__ inline void load_record(const void* __restrict__ feat, uint32_t g, float4& a, float4& b, float& c)
+{
+    if (REC == 0) {
+        const float4* f = (const float4*)feat + 3 * (size_t)g;
+        a = f[0];
+        b = f[1];
+        c = f[2].x;
+    } else {
+        const uint2* f = (const uint2*)feat + 3 * (size_t)g;
+        const uint2 w0 = f[0], w1 = f[1], w2 = f[2];
+        __half2 ab, co;
+        __nv_bfloat162 rg;
+        memcpy(&ab, &w1.x, 4);
+        memcpy(&co, &w1.y, 4);
+        memcpy(&rg, &w2.x, 4);
+        const float2 fab = __half22float2(ab), fco = __half22float2(co), frg = __bfloat1622float2(rg);
+        a = make_float4(__uint_as_float(w0.x), __uint_as_float(w0.y), fab.x, fab.y);
+        b = make_float4(fco.x, fco.y, frg.x, frg.y);
+        c = __uint_as_float(w2.y << 16);  // bfloat16 in the low half: its float32 is the bits shifted up
+    }
 }
 
 // Views of one launch: image sizes, tile grids and where each view's tiles and
@@ -290,9 +322,9 @@ __device__ inline Item next_item(int* counter, int count, const int4* list, cons
 // the chunk's (1 - alpha) factors from 1, no colour).  Otherwise Eq. 1 over
 // the item's entries from T_in, writing the final pixels (whole tile) or the
 // chunk's slot (split tile).
-template <int B, int PPT, bool PROD>
+template <int B, int PPT, bool PROD, int REC>
 __global__ void __launch_bounds__(B * B / PPT)
-k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
+k_render_fwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
              const uint2* __restrict__ ranges, RViews rv, RHdr* hdr, const int4* __restrict__ items,
              const int4* __restrict__ sitems, Slots sl,
              float* __restrict__ img, float* __restrict__ Tout, int* __restrict__ lastout,
@@ -355,9 +387,7 @@ k_render_fwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
         float gc = 0.f;
         if (j < hi) {
             const uint32_t g = gid[rg.x + j];
-            ga = feat[3 * (size_t)g];
-            gb = feat[3 * (size_t)g + 1];
-            gc = feat[3 * (size_t)g + 2].x;
+            load_record<REC>(feat, g, ga, gb, gc);
             keep = !tile_skip(ga, gb, tpx0, tpx1, tpy0, tpy1);
         }
         int cnt;
@@ -545,9 +575,9 @@ __device__ inline float warp_sum9(const float v[9], int lane, int* idx)
     return a4;
 }
 
-template <int B, int PPT>
+template <int B, int PPT, int REC>
 __global__ void __launch_bounds__(B * B / PPT)
-k_render_bwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
+k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
              const uint2* __restrict__ ranges, RViews rv, RHdr* hdr, const int4* __restrict__ items, Slots sl,
              const float* __restrict__ Tfin, const int* __restrict__ lastin,
              const float* __restrict__ dLdimg, float4* __restrict__ grad2d)
@@ -628,9 +658,7 @@ k_render_bwd(const float4* __restrict__ feat, const uint32_t* __restrict__ gid,
         uint32_t g = 0;
         if (j < top) {
             g = gid[rg.x + j];
-            ga = feat[3 * (size_t)g];
-            gb = feat[3 * (size_t)g + 1];
-            gc = feat[3 * (size_t)g + 2].x;
+            load_record<REC>(feat, g, ga, gb, gc);
             keep = !tile_skip(ga, gb, tpx0, tpx1, tpy0, tpy1);
         }
         int cnt;
@@ -788,13 +816,13 @@ static RenderWs render_ws(void* base, long long n_tiles, int B, bool split)
     return w;
 }
 
-template <int B, int PPT>
+template <int B, int PPT, int REC>
 static dg_status launch_fwd(const float* feat, const uint32_t* gid, const uint32_t* ranges, const dg::RViews& rv,
                             const RenderWs& w, int split_req, float* img, float* T, int* last, int* ex, int* bl,
                             cudaStream_t s)
 {
     const uint2* rg = (const uint2*)ranges;
-    auto kern = dg::k_render_fwd<B, PPT, false>;
+    auto kern = dg::k_render_fwd<B, PPT, false, REC>;
     const int R = resident_ctas(kern, B * B / PPT);
     cudaMemsetAsync(w.hdr, 0, 256, s);
     // automatic: split only when the tiles alone leave resident CTAs idle
@@ -811,13 +839,13 @@ static dg_status launch_fwd(const float* feat, const uint32_t* gid, const uint32
         dg::exclusive_scan(dg::LoadChunks{rg, w.hdr, cfg}, n, w.toff, w.bsum, &w.hdr->totals, s);
         const int pg = (int)((n + 255) / 256);
         dg::k_plan_items<<<pg < 1024 ? pg : 1024, 256, 0, s>>>(rg, (int)n, w.hdr, cfg, w.toff, w.items, w.sitems);
-        auto kprod = dg::k_render_fwd<B, PPT, true>;
+        auto kprod = dg::k_render_fwd<B, PPT, true, REC>;
         kprod<<<resident_ctas(kprod, B * B / PPT), B * B / PPT, 0, s>>>(
-            (const float4*)feat, gid, rg, rv, w.hdr, w.items, w.sitems, w.sl, img, T, last, ex, bl);
+            (const void*)feat, gid, rg, rv, w.hdr, w.items, w.sitems, w.sl, img, T, last, ex, bl);
         dg_note_launch(2);
     }
     const int grid = split ? R : (R < rv.total ? R : (rv.total > 0 ? rv.total : 1));
-    kern<<<grid, B * B / PPT, 0, s>>>((const float4*)feat, gid, rg, rv, w.hdr, w.items, w.sitems, w.sl, img, T,
+    kern<<<grid, B * B / PPT, 0, s>>>((const void*)feat, gid, rg, rv, w.hdr, w.items, w.sitems, w.sl, img, T,
                                       last, ex, bl);
     dg_note_launch();
     if (split) {
@@ -831,16 +859,40 @@ static dg_status launch_fwd(const float* feat, const uint32_t* gid, const uint32
     return DG_OK;
 }
 
-template <int B, int PPT>
+template <int B, int PPT, int REC>
 static void launch_bwd(const float* feat, const uint32_t* gid, const uint32_t* ranges, const dg::RViews& rv,
                        const RenderWs& w, const float* T, const int* last, const float* dL, float* g2, cudaStream_t s)
 {
-    auto kern = dg::k_render_bwd<B, PPT>;
+    auto kern = dg::k_render_bwd<B, PPT, REC>;
     const int grid = resident_ctas(kern, B * B / PPT);
     cudaMemsetAsync(&w.hdr->cnt_bwd, 0, sizeof(int), s);
-    kern<<<grid, B * B / PPT, 0, s>>>((const float4*)feat, gid, (const uint2*)ranges, rv, w.hdr, w.items, w.sl, T,
+    kern<<<grid, B * B / PPT, 0, s>>>((const void*)feat, gid, (const uint2*)ranges, rv, w.hdr, w.items, w.sl, T,
                                       last, dL, (float4*)g2);
     dg_note_launch();
+}
+
+template <int REC>
+static void fwd_dispatch(int B, int ppt, const float* feat, const uint32_t* gid, const uint32_t* ranges,
+                         const dg::RViews& rv, const RenderWs& w, int sp, float* img, float* T, int* last, int* ex,
+                         int* bl, cudaStream_t s)
+{
+    if (B == 8 && ppt == 2) launch_fwd<8, 2, REC>(feat, gid, ranges, rv, w, sp, img, T, last, ex, bl, s);
+    else if (B == 8) launch_fwd<8, 1, REC>(feat, gid, ranges, rv, w, sp, img, T, last, ex, bl, s);
+    else if (ppt == 1) launch_fwd<16, 1, REC>(feat, gid, ranges, rv, w, sp, img, T, last, ex, bl, s);
+    else if (ppt == 2) launch_fwd<16, 2, REC>(feat, gid, ranges, rv, w, sp, img, T, last, ex, bl, s);
+    else launch_fwd<16, 4, REC>(feat, gid, ranges, rv, w, sp, img, T, last, ex, bl, s);
+}
+
+template <int REC>
+static void bwd_dispatch(int B, int ppt, const float* feat, const uint32_t* gid, const uint32_t* ranges,
+                         const dg::RViews& rv, const RenderWs& w, const float* T, const int* last, const float* dL,
+                         float* g2, cudaStream_t s)
+{
+    if (B == 8 && ppt == 2) launch_bwd<8, 2, REC>(feat, gid, ranges, rv, w, T, last, dL, g2, s);
+    else if (B == 8) launch_bwd<8, 1, REC>(feat, gid, ranges, rv, w, T, last, dL, g2, s);
+    else if (ppt == 1) launch_bwd<16, 1, REC>(feat, gid, ranges, rv, w, T, last, dL, g2, s);
+    else if (ppt == 2) launch_bwd<16, 2, REC>(feat, gid, ranges, rv, w, T, last, dL, g2, s);
+    else launch_bwd<16, 4, REC>(feat, gid, ranges, rv, w, T, last, dL, g2, s);
 }
 
 // Pixels per thread used for (tile, request): tile 16 -> 1, 2 or 4 (0 selects
@@ -871,6 +923,7 @@ static bool render_args(const dg_camera* cams, int n_views, const dg_raster_opts
     const int p = opts->pixels_per_thread;
     if (p != 0 && p != 1 && p != 2 && p != 4) { dg_set_error("pixels_per_thread must be 0, 1, 2 or 4, got %d", p); return false; }
     if (total_tiles(cams, n_views, opts->tile) >= (1LL << 30)) { dg_set_error("too many tiles"); return false; }
+    if (opts->record != 0 && opts->record != 1) { dg_set_error("record must be 0 (float32) or 1 (mixed), got %d", opts->record); return false; }
     const size_t need = dg_render_workspace_size(cams, n_views, opts);
     if (!ws || ws_bytes < need) { dg_set_error("render workspace missing or too small (%zu < %zu bytes)", ws_bytes, need); return false; }
     if (((uintptr_t)ws) & 255u) { dg_set_error("render workspace must be 256-byte aligned"); return false; }
@@ -899,11 +952,8 @@ extern "C" dg_status dg_render_fwd(const float* feat, const uint32_t* gid, const
     const RenderWs w = render_ws(ws, rv.total, B, opts->split_len >= 0);
     const int sp = opts->split_len;
     const int ppt = resolve_ppt(opts, false);
-    if (B == 8 && ppt == 2) launch_fwd<8, 2>(feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
-    else if (B == 8) launch_fwd<8, 1>(feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
-    else if (ppt == 1) launch_fwd<16, 1>(feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
-    else if (ppt == 2) launch_fwd<16, 2>(feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
-    else launch_fwd<16, 4>(feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
+    if (opts->record == 1) fwd_dispatch<1>(B, ppt, feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
+    else fwd_dispatch<0>(B, ppt, feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
     return dg_check_launch("render_fwd");
 }
 
@@ -922,10 +972,7 @@ extern "C" dg_status dg_render_bwd(const float* feat, const uint32_t* gid, const
     const dg::RViews rv = make_rviews(cams, n_views, B, opts);
     const RenderWs w = render_ws(ws, rv.total, B, opts->split_len >= 0);
     const int ppt = resolve_ppt(opts, true);
-    if (B == 8 && ppt == 2) launch_bwd<8, 2>(feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
-    else if (B == 8) launch_bwd<8, 1>(feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
-    else if (ppt == 1) launch_bwd<16, 1>(feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
-    else if (ppt == 2) launch_bwd<16, 2>(feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
-    else launch_bwd<16, 4>(feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
+    if (opts->record == 1) bwd_dispatch<1>(B, ppt, feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
+    else bwd_dispatch<0>(B, ppt, feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
     return dg_check_launch("render_bwd");
 }

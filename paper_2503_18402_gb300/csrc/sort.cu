@@ -35,10 +35,18 @@ __global__ void k_depth_keys(const float* __restrict__ depth, const int* __restr
 }
 
 // view index of each depth-ordered record, for the stable view pass
-__global__ void k_view_keys(const uint32_t* __restrict__ rec, long long N, uint32_t P, uint32_t* __restrict__ keys)
+// View key of the record at sorted position i: its view, or n_views for a
+// culled record, so that every culled record (no pairs) ends up behind all
+// visible records of all views.  (Left between two views, runs of culled
+// records would fill k_emit's window of staged Gaussians.)
+__global__ void k_view_keys(const uint32_t* __restrict__ rec, const int* __restrict__ tiles, long long N, uint32_t P,
+                            uint32_t n_views, uint32_t* __restrict__ keys)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) keys[i] = rec[i] / P;
+    if (i < N) {
+        const uint32_t r = rec[i];
+        keys[i] = tiles[r] > 0 ? r / P : n_views;
+    }
 }
 
 struct TileGrid {
@@ -71,6 +79,7 @@ k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const ui
        const long long* M_dev, long long M_cap, int B, TileGrid tg, uint32_t mask0, uint32_t* __restrict__ pkey,
        uint32_t* __restrict__ pval, uint32_t* __restrict__ hist0, int nblk, int* status)
 {
+    const uint32_t n_tiles = (uint32_t)tg.off[tg.n];
     __shared__ int w_start[RS_TILE];      // pair offset of each staged Gaussian, relative to the block
     __shared__ uint32_t w_xy[RS_TILE];    // rect x0 | y0 << 16
     __shared__ int w_wx[RS_TILE];         // rect width in tiles
@@ -83,7 +92,7 @@ k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const ui
         if (blockIdx.x == 0 && threadIdx.x == 0) *status = DG_ERR_CAPACITY;
         return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *status = DG_OK;
+    // (status was cleared by the host before this launch; blocks only set errors)
     __shared__ int s_nw;
     for (int d = threadIdx.x; d < (1 << RS_MAXBITS); d += RS_THREADS) h[d] = 0;
     if (threadIdx.x == 0) s_nw = 0;
@@ -143,7 +152,11 @@ k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const ui
                         next = lo + 1 < nw ? w_start[lo + 1] : nblock;
                         rx = 0; ry = 0;
                     }
-                    const uint32_t key = (uint32_t)(tb + ((int)(xy >> 16) + ry) * TXv + (int)(xy & 0xffffu) + rx);
+                    uint32_t key = (uint32_t)(tb + ((int)(xy >> 16) + ry) * TXv + (int)(xy & 0xffffu) + rx);
+                    if (key >= n_tiles) {  // cannot happen for consistent inputs; never index past the grid
+                        *status = DG_ERR_CUDA;
+                        key = 0;
+                    }
                     kk[e] = key;
                     vv[e] = g;
                     atomicAdd(&h[key & mask0], 1u);
@@ -286,10 +299,10 @@ extern "C" dg_status dg_bin_count(const float* depth, const int32_t* tiles, int6
     if (r.v != w.dv0) { dg_set_error("internal: depth order buffer"); return DG_ERR_CUDA; }
     if (n_views > 1) {
         // stable pass on the view index: (view, depth, index), result in dv1
-        dg::k_view_keys<<<nb, 256, 0, s>>>(w.dv0, N, (uint32_t)P, w.dk1);
+        dg::k_view_keys<<<nb, 256, 0, s>>>(w.dv0, tiles, N, (uint32_t)P, (uint32_t)n_views, w.dk1);
         dg_note_launch();
         const dg::KV r2 = dg::radix_sort(w.dk1, w.dv0, w.dk0, w.dv1, nullptr, nullptr, nullptr, N,
-                                         dg::view_bits(n_views), sb, s);
+                                         dg::view_bits(n_views + 1), sb, s);
         if (r2.v != w.dv1) { dg_set_error("internal: view order buffer"); return DG_ERR_CUDA; }
     }
     dg::exclusive_scan(dg::LoadTilesInOrder{tiles, dg::order_buffer(w, n_views)}, N, w.poff, w.bsum, w.M, s);

@@ -51,10 +51,16 @@ class StepGraph:
         hp_bytes = ctypes.sizeof(capi.AdamHparams)
         self.cams_dev = torch.empty(cam_bytes, dtype=torch.uint8, device=d)
         self.hp_dev = torch.empty(hp_bytes, dtype=torch.uint8, device=d)
-        self.cams_host = torch.empty(cam_bytes, dtype=torch.uint8).pin_memory()
-        self.hp_host = torch.empty(hp_bytes, dtype=torch.uint8).pin_memory()
-        self.out_host = torch.zeros(2, dtype=torch.int64).pin_memory()  # status, pair count
-        self.out_event = None
+        # two pinned staging slots: the host fills one while the copies of the
+        # previous step may still read the other
+        self.cams_host = [torch.empty(cam_bytes, dtype=torch.uint8).pin_memory() for _ in range(2)]
+        self.hp_host = [torch.empty(hp_bytes, dtype=torch.uint8).pin_memory() for _ in range(2)]
+        self.slot_event = [torch.cuda.Event(), torch.cuda.Event()]
+        self.slot = 0
+        # per staging slot: (status, pair count) of the step that used the slot
+        self.out_host = [torch.zeros(2, dtype=torch.int64).pin_memory() for _ in range(2)]
+        self.out_event = [torch.cuda.Event(), torch.cuda.Event()]
+        self.status64 = torch.zeros(1, dtype=torch.int64, device=d)
         self.params, self.m, self.v, self.grads, self.stride = params, m, v, grads, stride
         self.lam = ssim_lambda
         self.stats = stats
@@ -76,48 +82,61 @@ class StepGraph:
         capi.dg_adam_step_dev(self.params, self.grads, self.m, self.v, self.stride, self.P, self.hp_dev,
                               skip_if=rz.status, stream=stream)
 
-    def _write_inputs(self, cams, hp: capi.AdamHparams, targets, stream):
-        arr = capi.cameras(cams)
-        ctypes.memmove(self.cams_host.data_ptr(), ctypes.addressof(arr), ctypes.sizeof(arr))
-        ctypes.memmove(self.hp_host.data_ptr(), ctypes.addressof(hp), ctypes.sizeof(hp))
+    def _write_inputs(self, cams, hp: capi.AdamHparams, targets, stream) -> int:
+        k = self.slot
+        self.slot = 1 - k
+        self.slot_event[k].synchronize()  # the copies that last read this slot are done
+        csz = ctypes.sizeof(capi.Camera)
+        base = self.cams_host[k].data_ptr()
+        for v, c in enumerate(cams):
+            ctypes.memmove(base + v * csz, ctypes.addressof(c), csz)
+        ctypes.memmove(self.hp_host[k].data_ptr(), ctypes.addressof(hp), ctypes.sizeof(hp))
         with torch.cuda.stream(stream):
-            self.cams_dev.copy_(self.cams_host, non_blocking=True)
-            self.hp_dev.copy_(self.hp_host, non_blocking=True)
+            self.cams_dev.copy_(self.cams_host[k], non_blocking=True)
+            self.hp_dev.copy_(self.hp_host[k], non_blocking=True)
+            self.slot_event[k].record(stream)
             off = 0
             for t in targets:
                 n = t.numel()
                 self.target[off: off + n].copy_(t.reshape(-1), non_blocking=True)
                 off += n
+        return k
 
-    def capture(self, cams, hp, targets):
-        """Warm-up run (which also performs a step), then capture."""
+    def capture(self, cams, hp, targets) -> int:
+        """Warm-up run (which also performs a step), then capture.  Returns the
+        slot holding that step's result (see result())."""
         s = torch.cuda.Stream(self.device)
         s.wait_stream(torch.cuda.current_stream(self.device))
-        self._write_inputs(cams, hp, targets, s)
+        k = self._write_inputs(cams, hp, targets, s)
         with torch.cuda.stream(s):
             self._sequence(s)
         torch.cuda.current_stream(self.device).wait_stream(s)
-        self._finish(torch.cuda.current_stream(self.device))
+        self._finish(torch.cuda.current_stream(self.device), k)
         g = torch.cuda.CUDAGraph()
         torch.cuda.synchronize(self.device)
         with torch.cuda.graph(g, stream=s):
             self._sequence(s)
         self.graph = g
+        return k
 
-    def replay(self, cams, hp, targets):
+    def replay(self, cams, hp, targets) -> int:
         stream = torch.cuda.current_stream(self.device)
-        self._write_inputs(cams, hp, targets, stream)
+        k = self._write_inputs(cams, hp, targets, stream)
         self.graph.replay()
-        self._finish(stream)
+        self._finish(stream, k)
+        return k
 
-    def _finish(self, stream):
+    def _finish(self, stream, k):
         with torch.cuda.stream(stream):
-            self.out_host[0:1].copy_(self.rz.status.to(torch.int64), non_blocking=True)
-            self.out_host[1:2].copy_(self.rz.M_dev, non_blocking=True)
-        self.out_event = torch.cuda.Event()
-        self.out_event.record(stream)
+            self.status64.copy_(self.rz.status)
+            self.out_host[k][0:1].copy_(self.status64, non_blocking=True)
+            self.out_host[k][1:2].copy_(self.rz.M_dev, non_blocking=True)
+        self.out_event[k].record(stream)
 
-    def result(self):
-        """(status, pair count) of the last step; waits for it."""
-        self.out_event.synchronize()
-        return int(self.out_host[0]), int(self.out_host[1])
+    def result(self, k=None):
+        """(status, pair count) of the step that used slot k (default: the
+        latest); waits for that step."""
+        if k is None:
+            k = 1 - self.slot
+        self.out_event[k].synchronize()
+        return int(self.out_host[k][0]), int(self.out_host[k][1])

@@ -86,6 +86,9 @@ class Rasterizer:
         self.tiles = torch.empty(n, dtype=torch.int32, device=d)
         self.clamp = torch.empty(n, dtype=torch.uint8, device=d)
         self.grad2d = torch.empty((n, capi.FEAT_FLOATS), dtype=torch.float32, device=d)
+        # mixed-precision copy of the records read by the render passes (opts.record == 1)
+        self.packed = (torch.empty(n * capi.PACKED_RECORD_BYTES, dtype=torch.uint8, device=d)
+                       if self.opts.record == 1 else None)
         self.M_dev = torch.zeros(1, dtype=torch.int64, device=d)
         self.status = torch.zeros(1, dtype=torch.int32, device=d)
         self.N_cap = N
@@ -98,6 +101,13 @@ class Rasterizer:
         if M_cap > self.M_cap or not hasattr(self, "gid"):
             self.gid = torch.empty(max(M_cap, 1), dtype=torch.int32, device=self.device)
             self.M_cap = M_cap
+
+    def _pack(self, n_records, stream):
+        """Render-side records: the float32 ones, or their mixed-precision packing."""
+        if self.opts.record == 1:
+            capi.dg_pack_records(self.feat, n_records, self.packed, stream)
+            return self.packed
+        return self.feat
 
     def _ensure_tiles(self, n_tiles):
         if n_tiles > self.n_tiles:
@@ -145,7 +155,8 @@ class Rasterizer:
         capi.dg_bin_sort(self.feat, self.radius, P, carr, V, B, self.ws, self.ws.numel(), self.M_cap, self.gid,
                          self.ranges, self.status, stream)
         f = self.fixed
-        capi.dg_render_fwd(self.feat, self.gid, self.ranges, carr, V, self.opts_fwd, f["img"], f["T"], f["last"],
+        self.rfeat = self._pack(V * P, stream)
+        capi.dg_render_fwd(self.rfeat, self.gid, self.ranges, carr, V, self.opts_fwd, f["img"], f["T"], f["last"],
                            None, None, self.rws, self.rws.numel(), stream)
         return Frame(P=P, cams=cams, img=f["img"], T=f["T"], last=f["last"], M=-1, flat_img=f["img"],
                      flat_T=f["T"], flat_last=f["last"])
@@ -190,7 +201,8 @@ class Rasterizer:
             ex = torch.empty(npix, dtype=torch.int32, device=self.device)
             bl = torch.empty(npix, dtype=torch.int32, device=self.device)
         self._ensure_rws(carr, V)
-        capi.dg_render_fwd(self.feat, self.gid, self.ranges, carr, V, self.opts_fwd, img, T, last, ex, bl,
+        self.rfeat = self._pack(V * P, stream)
+        capi.dg_render_fwd(self.rfeat, self.gid, self.ranges, carr, V, self.opts_fwd, img, T, last, ex, bl,
                            self.rws, self.rws.numel(), stream)
         self._mark("render_fwd")
         fr = Frame(P=P, cams=cams, img=img, T=T, last=last, M=M, flat_img=img, flat_T=T, flat_last=last)
@@ -218,7 +230,7 @@ class Rasterizer:
         assert dL_dimg.numel() == fr.flat_img.numel()
         carr = capi.cameras(fr.cams)
         V = len(fr.cams)
-        capi.dg_render_bwd(self.feat, self.gid, self.ranges, carr, V, self.opts_bwd, fr.flat_T, fr.flat_last,
+        capi.dg_render_bwd(self.rfeat, self.gid, self.ranges, carr, V, self.opts_bwd, fr.flat_T, fr.flat_last,
                            dL_dimg, V * fr.P, self.grad2d, self.rws, self.rws.numel(), stream)
         self._mark("render_bwd")
 
@@ -242,7 +254,7 @@ class Rasterizer:
         assert dL_dimg.numel() == fr.flat_img.numel()
         carr = capi.cameras(fr.cams)
         V = len(fr.cams)
-        capi.dg_render_bwd(self.feat, self.gid, self.ranges, carr, V, self.opts_bwd, fr.flat_T, fr.flat_last,
+        capi.dg_render_bwd(self.rfeat, self.gid, self.ranges, carr, V, self.opts_bwd, fr.flat_T, fr.flat_last,
                            dL_dimg, V * fr.P, self.grad2d, self.rws, self.rws.numel(), stream)
         self._mark("render_bwd")
         capi.dg_project_bwd(params, params.stride(0), fr.P, carr, V, self.opts, self.radius, self.clamp,

@@ -80,6 +80,9 @@ class TrainConfig:
     # the whole step in a CUDA graph (replayed with new cameras / LR / targets)
     views_per_step: int = 1
     cuda_graph: bool = False
+    # records read by the render passes: 0 float32, 1 mixed (float16 conic and
+    # opacity, bfloat16 colour; float32 transmittance, sums and gradients)
+    record: int = 0
     # projection adjoint fused with the Adam update (no stored gradient); off:
     # the fused kernel's register footprint (one thread per Gaussian holding all
     # 59 gradients) leaves too few warps resident to stream params, m and v
@@ -108,7 +111,8 @@ class Trainer:
         self.acc = torch.zeros(cap, **f32)
         self.den = torch.zeros(cap, **f32)
         self.maxr = torch.zeros(cap, **f32)
-        self.tuner = RenderTuner(self.dev, capi.raster_opts(), fixed=None if cfg.autotune else Shape(16, 2, 4, 0))
+        self.tuner = RenderTuner(self.dev, capi.raster_opts(record=cfg.record),
+                                 fixed=None if cfg.autotune else Shape(16, 2, 4, 0))
         self.rz = self.tuner.rasterizer(Shape(8, 1, 1, 0))  # evaluation renders
         n_full = 3 * self.H * self.W
         self.dL = torch.empty(n_full, **f32)
@@ -129,9 +133,10 @@ class Trainer:
         self.init_schedule_s = 0.0
         self.densify_until = cfg.densify_until
         self.graphs = {}
+        self._cam_cache = {}
         self.graph_P = -1
         self.M_hint = {}
-        self.pending = None  # (StepGraph) whose status is read one step later
+        self.pending = []  # replayed steps whose status is still to be read
         self.skipped_steps = 0
         self.graph_captures = 0
 
@@ -170,10 +175,16 @@ class Trainer:
         return t
 
     def _camera(self, j, h, w):
-        v = self.views[j]
-        fx, fy, cx, cy = v["intr"]
-        sx, sy = w / self.W, h / self.H
-        return make_camera(np.asarray(v["viewmat"], np.float32).reshape(-1), (fx * sx, fy * sy, cx * sx, cy * sy), w, h)
+        key = (j, h, w)
+        c = self._cam_cache.get(key)
+        if c is None:
+            v = self.views[j]
+            fx, fy, cx, cy = v["intr"]
+            sx, sy = w / self.W, h / self.H
+            c = make_camera(np.asarray(v["viewmat"], np.float32).reshape(-1), (fx * sx, fy * sy, cx * sx, cy * sy),
+                            w, h)
+            self._cam_cache[key] = c
+        return c
 
     def _next_view(self):
         if not self.order:
@@ -217,16 +228,10 @@ class Trainer:
             capi.dg_adam_step(b["p"], self.grads, b["m"], b["v"], self.cap, P, lr, 0.9, 0.999, 1e-15, k + 1,
                               self.stream)
             return r, fr.M
-        # graph path: one graph per (P, size, stats window, buffer set); read the
-        # previous step's status one step late (no wait inside the loop)
-        if self.pending is not None:
-            g_prev = self.pending
-            status, M = g_prev.result()
-            sz = g_prev.sizes[0]
-            self.M_hint[sz] = max(self.M_hint.get(sz, 0), M)
-            if status != 0:  # pair capacity exceeded: that step made no update
-                self.skipped_steps += 1
-                self.graphs.pop(g_prev.key, None)
+        # graph path: one graph per (P, size, stats window, buffer set); the
+        # status of a step is read two steps later, so the host prepares the
+        # next step while the GPU runs the current one
+        self._check_pending(keep=1)
         if P != self.graph_P:
             self.graphs.clear()
             self.graph_P = P
@@ -240,17 +245,29 @@ class Trainer:
                 fr0 = rz0.forward(b["p"][:, :P], P, cams, self.stream)
                 hint = fr0.M
             M_cap = int(hint * 1.5) + 4096
-            g = StepGraph(self.dev, capi.raster_opts(tile=8), 1, 1, b["p"], b["m"], b["v"], self.grads, self.cap, P,
+            g = StepGraph(self.dev, capi.raster_opts(tile=8, record=cfg.record), 1, 1, b["p"], b["m"], b["v"],
+                          self.grads, self.cap, P,
                           cams, M_cap, cfg.ssim_lambda, (self.acc, self.den, self.maxr) if stats_on else None)
             g.key = key
-            g.capture(cams, hp, targets)
+            slot = g.capture(cams, hp, targets)
             self.graphs[key] = g
             self.graph_captures += 1
         else:
-            g.replay(cams, hp, targets)
-        self.pending = g
+            slot = g.replay(cams, hp, targets)
+        self.pending.append((g, slot))
         self.loss = g.loss
         return r, -1
+
+    def _check_pending(self, keep):
+        """Reads the status of all but the last `keep` replayed steps."""
+        while len(self.pending) > keep:
+            g_prev, slot = self.pending.pop(0)
+            status, M = g_prev.result(slot)
+            sz = g_prev.sizes[0]
+            self.M_hint[sz] = max(self.M_hint.get(sz, 0), M)
+            if status != 0:  # pair capacity exceeded: that step made no update
+                self.skipped_steps += 1
+                self.graphs.pop(g_prev.key, None)
 
     def dL_b(self, n):
         if getattr(self, "_dLb", None) is None or self._dLb.numel() < n:
@@ -271,7 +288,19 @@ class Trainer:
     def step(self, k):
         cfg = self.cfg
         if cfg.views_per_step > 1 or cfg.cuda_graph:
-            return self._step_batched(k)
+            r, M = self._step_batched(k)
+        else:
+            r, M = self._step_single(k)
+        kk = k + 1
+        if cfg.densify_from <= kk <= self.densify_until and kk % cfg.densify_every == 0:
+            self.densify(kk)
+        if kk % cfg.opacity_reset_every == 0 and kk <= cfg.densify_until:
+            b = self.buf[self.cur]
+            capi.dg_opacity_reset(b["p"], b["m"], b["v"], self.cap, self.P, 0.01, self.stream)
+        return r, M
+
+    def _step_single(self, k):
+        cfg = self.cfg
         b = self.buf[self.cur]
         P = self.P
         r, h, w, lr_pos = self._plan(k)
@@ -301,12 +330,6 @@ class Trainer:
                                 self.grads[:, :P], self.stream)
             capi.dg_adam_step(b["p"], self.grads, b["m"], b["v"], self.cap, P, lr, 0.9, 0.999, 1e-15, k + 1,
                               self.stream)
-        kk = k + 1
-        if cfg.densify_from <= kk <= self.densify_until and kk % cfg.densify_every == 0:
-            self.densify(kk)
-        if kk % cfg.opacity_reset_every == 0 and kk <= cfg.densify_until:
-            b = self.buf[self.cur]
-            capi.dg_opacity_reset(b["p"], b["m"], b["v"], self.cap, self.P, 0.01, self.stream)
         return r, fr.M
 
     def densify(self, k):
@@ -318,8 +341,11 @@ class Trainer:
         if self.dws is None or self.dws.numel() < need:
             self.dws = torch.empty(int(need * 1.2) + 1024, dtype=torch.uint8, device=self.dev)
         big = cfg.big_point_prune and k > cfg.opacity_reset_every
-        opts = capi.densify_opts(cfg.grad_thresh, cfg.min_opacity, cfg.percent_dense, cfg.extent,
-                                 20.0 if big else 0.0, 0.1 * cfg.extent if big else 0.0)
+        # the loss of a V-view step is the mean over its views, so each view's
+        # screen-space gradient carries a factor 1/V: the per-view threshold
+        # scales with it
+        opts = capi.densify_opts(cfg.grad_thresh / cfg.views_per_step, cfg.min_opacity, cfg.percent_dense,
+                                 cfg.extent, 20.0 if big else 0.0, 0.1 * cfg.extent if big else 0.0)
         capi.dg_densify_mark(b["p"], self.cap, P, self.acc, self.den, self.maxr, opts, self.dws, self.dws.numel(),
                              self.counts, self.stream)
         n_keep, n_cand = (int(x) for x in self.counts.cpu())
@@ -365,9 +391,7 @@ class Trainer:
                 print(json.dumps(dict(iter=k + 1, P=self.P, r=r, loss=float(self.loss[0].item()),
                                       s=round(time.perf_counter() - t0, 2))), flush=True)
         torch.cuda.synchronize()
-        if self.pending is not None:
-            status, _ = self.pending.result()
-            self.skipped_steps += int(status != 0)
+        self._check_pending(keep=0)
         return dict(seconds=time.perf_counter() - t0, schedule_init_s=self.init_schedule_s, P_final=self.P,
                     iters_per_factor={str(k): v for k, v in sorted(res_hist.items())},
                     render_shapes=self.tuner.summary(), views_per_step=cfg.views_per_step,
@@ -411,6 +435,8 @@ def main(argv=None):
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--views-per-step", type=int, default=1)
     ap.add_argument("--cuda-graph", action="store_true", help="capture each step in a CUDA graph")
+    ap.add_argument("--record", choices=["fp32", "mixed"], default="fp32",
+                    help="render-side record storage (mixed: float16 conic/opacity, bfloat16 colour)")
     args = ap.parse_args(argv)
     from . import synth
     dev = torch.device("cuda")
@@ -422,7 +448,8 @@ def main(argv=None):
         cfg = TrainConfig(iters=args.iters, scheduled=(arm != "plain"), P_cap=args.p_cap,
                           reso_sched=arm in ("scheduled", "reso"), prim_sched=arm in ("scheduled", "prim"),
                           a=args.a, gamma=args.gamma, ssim_lambda=args.ssim_lambda, autotune=not args.no_autotune,
-                          views_per_step=args.views_per_step, cuda_graph=args.cuda_graph)
+                          views_per_step=args.views_per_step, cuda_graph=args.cuda_graph,
+                          record=1 if args.record == "mixed" else 0)
         if args.iters < 30000:  # compress the backbone's iteration windows proportionally
             s = args.iters / 30000
             cfg.densify_from = max(1, int(500 * s)); cfg.densify_until = int(15000 * s)

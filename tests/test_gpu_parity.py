@@ -234,6 +234,40 @@ def test_pixels_per_thread_variants(ppt, W, H):
     assert ok, (worst, nbad)
 
 
+def test_batched_views_with_many_culled_records():
+    """Views that each cull thousands of records: batched binning must equal
+    per-view binning (pair lists, ranges) and the oracle's order."""
+    g = synth.random_gaussians(20000, 77)
+    g[:, 0:3] *= 3.0  # spread beyond every view's frustum
+    sizes = [(40, 30), (48, 32), (40, 30), (56, 24), (40, 30), (32, 40)]
+    cams = [synth.camera_cfg0(W, H, 3.0 + 0.2 * i) for i, (W, H) in enumerate(sizes)]
+    P = g.shape[0]
+    params = G.gpu_params(g)
+    gcams = [G.gpu_camera(c) for c in cams]
+    opts = capi.raster_opts(tile=8)
+    rzb = Rasterizer("cuda", opts)
+    frb = rzb.forward(params, P, gcams)
+    torch.cuda.synchronize()
+    assert int(G.np_(rzb.status)[0]) == 0
+    radius = G.np_(rzb.radius[: len(sizes) * P]).reshape(len(sizes), P)
+    assert ((radius == 0).sum(axis=1) > 4096).all()  # more culled records per view than one emit window
+    gid = G.np_(rzb.gid[: frb.M]).view(np.uint32)
+    ranges = G.np_(rzb.ranges[: rzb.n_tiles]).view(np.uint32)
+    t0 = 0
+    for v, (c, (W, H)) in enumerate(zip(gcams, sizes)):
+        rz = Rasterizer("cuda", opts)
+        fr = rz.forward(params, P, c)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(G.np_(frb.images[v]), G.np_(fr.img))
+        nt = ((W + 7) // 8) * ((H + 7) // 8)
+        rg = ranges[t0: t0 + nt]
+        gid1 = G.np_(rz.gid[: fr.M]).view(np.uint32)
+        rg1 = G.np_(rz.ranges[:nt]).view(np.uint32)
+        for t in range(nt):
+            np.testing.assert_array_equal(gid[rg[t, 0]: rg[t, 1]] - v * P, gid1[rg1[t, 0]: rg1[t, 1]])
+        t0 += nt
+
+
 # ---------------------------------------------------------------- split lists
 def _render_split(g, cam, tile, split, bg, ppt=None):
     opts = capi.raster_opts(tile=tile, bg=bg, split_len=split)
