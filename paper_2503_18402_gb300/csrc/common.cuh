@@ -73,13 +73,27 @@ __device__ inline Rect tile_rect(float u, float v, int r, int B, int TX, int TY)
 // learning rate, betas, bias corrections 1 - b1^t and sqrt(1 - b2^t), epsilon.
 using AdamHp = dg_adam_hparams;
 
+// Per-row constants of the update: step size lr / (1 - b1^t) and 1 / sqrt(1 - b2^t).
+struct AdamRowK { float step, inv_bc2; };
+__device__ __forceinline__ AdamRowK adam_row(float lr, const AdamHp& h)
+{
+    return AdamRowK{lr / h.bc1, 1.f / h.bc2_sqrt};
+}
+
 // One Adam update of a scalar parameter (shared by the standalone and the fused
-// kernels so that both give the same bits).
-__device__ __forceinline__ void adam_update(float& p, float& m, float& v, float g, float lr, const AdamHp& h)
+// kernels so that both give the same bits):
+//   m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
+//   p <- p - step * m / (sqrt(v) / sqrt(1 - b2^t) + eps).
+// The square root and the division use the hardware approximations (a few ulp;
+// the update is a ratio of float32 moment estimates, far coarser than that):
+// the exact-rounded forms cost most of the kernel's issue slots.
+__device__ __forceinline__ void adam_update(float& p, float& m, float& v, float g, const AdamRowK& r,
+                                            const AdamHp& h)
 {
     m = fmaf(h.beta1, m, (1.f - h.beta1) * g);
     v = fmaf(h.beta2, v, (1.f - h.beta2) * (g * g));
-    p -= (lr / h.bc1) * m / (sqrtf(v) / h.bc2_sqrt + h.eps);
+    const float sv = v >= 1e-30f ? v * rsqrtf(v) : sqrtf(v);  // exact path for tiny (also subnormal) v
+    p -= __fdividef(r.step * m, fmaf(sv, r.inv_bc2, h.eps));
 }
 
 }  // namespace dg

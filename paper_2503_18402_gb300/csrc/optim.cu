@@ -95,7 +95,7 @@ k_adam(float* __restrict__ prm, const float* __restrict__ grd, float* __restrict
     if (i0 >= P) return;
     if (skip_if && *skip_if != 0) return;  // e.g. the step's pair list overflowed: no update
     const AdamHp& hp = hp_dev ? *hp_dev : hp_val;
-    const float lr = hp.lr[row];
+    const AdamRowK lr = adam_row(hp.lr[row], hp);
     const long long o = (long long)row * stride + i0;
     const bool vec = ((o & 3) == 0) && (i0 + 3 < P) && ((((uintptr_t)prm) & 15u) == 0) &&
                      ((((uintptr_t)grd) & 15u) == 0) && ((((uintptr_t)m) & 15u) == 0) &&

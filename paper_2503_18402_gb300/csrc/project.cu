@@ -292,7 +292,7 @@ k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host,
         if (grads) grads[o] = gval;
         if (ADAM) {
             float p = prm[o], mm = am[o], vv = av[o];
-            adam_update(p, mm, vv, gval, hp.lr[row], hp);
+            adam_update(p, mm, vv, gval, adam_row(hp.lr[row], hp), hp);
             prm[o] = p;
             am[o] = mm;
             av[o] = vv;

@@ -71,12 +71,14 @@ __device__ inline float quad_min_box(float A, float B, float C, float dxl, float
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         float dx, dy;
+        // (the minimiser only has to be near the edge's minimum: the form is
+        // flat there, so the fast division changes f by a second-order amount)
         if (e < 2) {
             dx = e ? dxh : dxl;
-            dy = fminf(fmaxf(-B * dx / C, dyl), dyh);
+            dy = fminf(fmaxf(__fdividef(-B * dx, C), dyl), dyh);
         } else {
             dy = (e & 1) ? dyh : dyl;
-            dx = fminf(fmaxf(-B * dy / A, dxl), dxh);
+            dx = fminf(fmaxf(__fdividef(-B * dy, A), dxl), dxh);
         }
         const float f = A * dx * dx + 2.f * B * dx * dy + C * dy * dy;
         const float mag = A * dx * dx + 2.f * fabsf(B * dx * dy) + C * dy * dy;
@@ -94,7 +96,7 @@ __device__ inline bool tile_skip(const float4& a, const float4& b, float px0, fl
     const float fmin = quad_min_box(a.z, a.w, b.x, a.x - px1, a.x - px0, a.y - py1, a.y - py0);
     // alpha = o exp(-fmin/2) < 1/255  <=>  fmin > 2 ln(255 o); 0.02 absorbs the
     // per-pixel rounding of the power and of exp
-    return fmin > 2.f * logf(255.f * o) + 0.02f;
+    return fmin > 2.f * __logf(255.f * o) + 0.02f;
 }
 
 // Pixel layout of a work item: warp w owns an 8-pixel-wide block of 4*PPT
@@ -124,10 +126,11 @@ constexpr float kLog2AlphaMin = -7.994353436858858f;
 
 // Backward: a warp whose contributing lanes number at most this many adds their
 // partial gradients with per-lane vector atomics instead of reducing first
-// (0: always reduce).  A launch-shape constant: results differ only in the
+// (0: always reduce; 16 measured fastest on the 2M-Gaussian full-resolution
+// step).  A launch-shape constant: results differ only in the
 // order of the float additions.
 #ifndef DG_BWD_DIRECT_LANES
-#define DG_BWD_DIRECT_LANES 0
+#define DG_BWD_DIRECT_LANES 16
 #endif
 constexpr int kBwdDirectLanes = DG_BWD_DIRECT_LANES;
 
@@ -399,42 +402,54 @@ k_render_fwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
             s_col[slot] = make_float4(gb.z, gb.w, gc, __int_as_float(j));
         }
         __syncthreads();
-        for (int kk = 0; kk < cnt && !alldone; ++kk) {
-            const float4 a = s_a[kk];
-            const float2 q = s_q[kk];
-            const float dx = a.x - pxc;
-            const float adx = a.z * dx;
-            alldone = true;
+        // Eq. 1 for entry kk at the thread's pixel k, given the entry's power p
+        // (log2 scale) and e = p + log2 o
+        auto blend = [&](int k, int kk, float p, float e) {
+            if (done[k] || !(p <= 0.f && e >= kLog2AlphaMin)) return;
+            const float alpha = fminf(kAlphaMax, ex2_approx(e));
+            const float Tn = fmaf(-alpha, T[k], T[k]);
+            const float4 col = s_col[kk];
+            const int pos = __float_as_int(col.w);
+            if (Tn < kTMin) {
+                done[k] = true;
+                stop[k] = pos;
+                if (PROD) T[k] = Tn;  // below the threshold: every later chunk is stopped
+            } else {
+                if (!PROD) {
+                    const float w = alpha * T[k];
+                    c0[k] += w * col.x;
+                    c1[k] += w * col.y;
+                    c2[k] += w * col.z;
+                    last[k] = pos + 1;
+                    ++nbl[k];
+                }
+                T[k] = Tn;
+            }
+        };
+        // two entries per iteration: their quadratic forms do not depend on the
+        // transmittance chain, so both are evaluated before either is blended
+        for (int kk = 0; kk < cnt && !alldone; kk += 2) {
+            const int k1 = kk + 1 < cnt ? kk + 1 : kk;
+            const float4 a0 = s_a[kk], a1 = s_a[k1];
+            const float2 q0 = s_q[kk], q1 = s_q[k1];
+            const float dx0 = a0.x - pxc, dx1 = a1.x - pxc;
+            const float adx0 = a0.z * dx0, adx1 = a1.z * dx1;
+            float p0[PPT], p1[PPT];
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-                if (!done[k]) {
-                    const float dy = a.y - pyc[k];
-                    const float p = fmaf(dx, fmaf(a.w, dy, adx), q.x * dy * dy);
-                    const float e = p + q.y;  // log2 of the unclamped alpha
-                    if (p <= 0.f && e >= kLog2AlphaMin) {
-                        const float alpha = fminf(kAlphaMax, ex2_approx(e));
-                        const float Tn = fmaf(-alpha, T[k], T[k]);
-                        const float4 col = s_col[kk];
-                        const int pos = __float_as_int(col.w);
-                        if (Tn < kTMin) {
-                            done[k] = true;
-                            stop[k] = pos;
-                            if (PROD) T[k] = Tn;  // below the threshold: every later chunk is stopped
-                        } else {
-                            if (!PROD) {
-                                const float w = alpha * T[k];
-                                c0[k] += w * col.x;
-                                c1[k] += w * col.y;
-                                c2[k] += w * col.z;
-                                last[k] = pos + 1;
-                                ++nbl[k];
-                            }
-                            T[k] = Tn;
-                        }
-                    }
-                }
-                alldone = alldone && done[k];
+                const float dy0 = a0.y - pyc[k], dy1 = a1.y - pyc[k];
+                p0[k] = fmaf(dx0, fmaf(a0.w, dy0, adx0), q0.x * dy0 * dy0);
+                p1[k] = fmaf(dx1, fmaf(a1.w, dy1, adx1), q1.x * dy1 * dy1);
             }
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) blend(k, kk, p0[k], p0[k] + q0.y);
+            if (k1 != kk) {
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) blend(k, k1, p1[k], p1[k] + q1.y);
+            }
+            alldone = true;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) alldone = alldone && done[k];
         }
     }
     if (split) {
