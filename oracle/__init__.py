@@ -47,7 +47,7 @@ class Consts(ctypes.Structure):
     _fields_ = [("near_plane", ctypes.c_double), ("eps2d", ctypes.c_double),
                 ("alpha_max", ctypes.c_double), ("alpha_min", ctypes.c_double),
                 ("t_min", ctypes.c_double), ("frustum_guard", ctypes.c_double),
-                ("tile", ctypes.c_int32), ("sh_degree", ctypes.c_int32)]
+                ("tile", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("mip2d", ctypes.c_double)]
 
 
 class Camera(ctypes.Structure):
@@ -58,9 +58,11 @@ class Camera(ctypes.Structure):
 
 
 def consts(tile=16, sh_degree=3, near_plane=0.2, eps2d=0.3, alpha_max=0.99,
-           alpha_min=1.0 / 255.0, t_min=1e-4, frustum_guard=1.3) -> Consts:
+           alpha_min=1.0 / 255.0, t_min=1e-4, frustum_guard=1.3, mip2d=0.0) -> Consts:
+    """mip2d > 0: Mip-Splatting's 2D filter (variance mip2d, opacity compensated)
+    in place of the eps2d dilation (the backbone variant of the supplementary)."""
     return Consts(near_plane, eps2d, alpha_max, alpha_min, t_min, frustum_guard,
-                  tile, sh_degree)
+                  tile, sh_degree, mip2d)
 
 
 def camera(viewmat, fx, fy, cx, cy, width, height) -> Camera:
@@ -243,6 +245,21 @@ def adam(param, grad, m, v, lr, beta1, beta2, eps, step):
     lr = _f64(np.broadcast_to(lr, param.shape))
     lib().dgo_adam(param.size, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), _ptr(lr),
                    beta1, beta2, eps, step)
+
+
+def sparse_adam(param, grad, m, v, lr, beta1, beta2, eps, step, visible):
+    """Sparse Adam of the Taming-3DGS backbone on planar [59][P] FP64 arrays:
+    the Adam update of ``adam`` on the columns (Gaussians) with visible != 0;
+    the other columns keep parameters and moments.  Global step count."""
+    vis = np.flatnonzero(np.asarray(visible) != 0)
+    if vis.size == 0:
+        return
+    lr = np.broadcast_to(np.asarray(lr, np.float64), param.shape)
+    sub = [np.ascontiguousarray(a[:, vis]) for a in (param, m, v)]
+    adam(sub[0], np.asarray(grad, np.float64)[:, vis], sub[1], sub[2], np.ascontiguousarray(lr[:, vis]),
+         beta1, beta2, eps, step)
+    for a, b in zip((param, m, v), sub):
+        a[:, vis] = b
 
 
 # --------------------------------------------------------------------------

@@ -51,6 +51,8 @@ typedef struct dgo_consts {
     double frustum_guard; /* clamp of t_x/t_z in the Jacobian, x half-FOV tan */
     int32_t tile;         /* tile edge B in pixels */
     int32_t sh_degree;    /* 0..3 */
+    double mip2d;         /* > 0: Mip-Splatting 2D filter of this variance in place of the
+                             dilation, opacity scaled by sqrt(det(S2) / det(S2 + mip2d I)) */
 } dgo_consts;
 
 typedef struct dgo_camera {
@@ -128,7 +130,9 @@ typedef struct gproj {
     double campos[3], draw[3], dlen, dir[3];
     double rgb[3];
     int clamp[3];
-    double o;
+    double osig;          /* sigmoid of the opacity logit */
+    double det0, comp;    /* 2D-filter opacity compensation sqrt(det0 / det) (1 without it) */
+    double o;             /* opacity of the record: osig * comp */
 } gproj;
 
 static int64_t floordiv(int64_t a, int64_t b) /* b > 0 */
@@ -191,11 +195,17 @@ static void project_one(const double* g, const dgo_camera* cam, const dgo_consts
                 for (int m = 0; m < 3; ++m) acc += P->T2[3 * i + l] * P->Sig[3 * l + m] * P->T2[3 * j + m];
             C2[2 * i + j] = acc;
         }
-    P->a = C2[0] + k->eps2d;
+    const double dil = k->mip2d > 0.0 ? k->mip2d : k->eps2d;
+    P->a = C2[0] + dil;
     P->b = C2[1];
-    P->c = C2[3] + k->eps2d;
+    P->c = C2[3] + dil;
     P->det = P->a * P->c - P->b * P->b;
     if (!(P->det > 0.0)) return;
+    P->comp = 1.0;
+    if (k->mip2d > 0.0) {
+        P->det0 = C2[0] * C2[3] - C2[1] * C2[1];
+        P->comp = P->det0 > 0.0 ? sqrt(P->det0 / P->det) : 0.0;
+    }
     P->conic[0] = P->c / P->det;
     P->conic[1] = -P->b / P->det;
     P->conic[2] = P->a / P->det;
@@ -236,7 +246,8 @@ static void project_one(const double* g, const dgo_camera* cam, const dgo_consts
         P->clamp[ch] = acc < 0.0;
         P->rgb[ch] = acc < 0.0 ? 0.0 : acc;
     }
-    P->o = 1.0 / (1.0 + exp(-g[O_OPAC]));
+    P->osig = 1.0 / (1.0 + exp(-g[O_OPAC]));
+    P->o = P->osig * P->comp;
     P->visible = 1;
 }
 
@@ -529,8 +540,8 @@ static void project_bwd_one(const double* g, const dgo_camera* cam, const dgo_co
     const double dd = P.dir[0] * dLddir[0] + P.dir[1] * dLddir[1] + P.dir[2] * dLddir[2];
     for (int i = 0; i < 3; ++i) dLdp[i] += (dLddir[i] - P.dir[i] * dd) / P.dlen;
 
-    /* opacity through the sigmoid */
-    out[O_OPAC] = g2[5] * P.o * (1.0 - P.o);
+    /* opacity through the sigmoid (and the 2D-filter compensation) */
+    out[O_OPAC] = g2[5] * P.comp * P.osig * (1.0 - P.osig);
 
     /* pixel mean */
     const double tx = P.t[0], ty = P.t[1], tz = P.t[2];
@@ -546,6 +557,18 @@ static void project_bwd_one(const double* g, const dgo_camera* cam, const dgo_co
         for (int j = 0; j < 2; ++j) KG[2 * i + j] = K[2 * i] * Gk[j] + K[2 * i + 1] * Gk[2 + j];
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) Gm[2 * i + j] = -(KG[2 * i] * K[j] + KG[2 * i + 1] * K[2 + j]);
+    /* 2D filter: comp = sqrt(det0 / det), det0 of T2 Sigma T2^T, det of it plus mip2d I;
+     * per matrix entry d det0 / dS00 = S11 (undilated), d det / dS00 = c (dilated), and
+     * the off-diagonal entry carries half of the derivative in b */
+    if (k->mip2d > 0.0 && P.det0 > 0.0) {
+        const double dLdc = g2[5] * P.osig;
+        const double a0 = P.a - k->mip2d, c0 = P.c - k->mip2d;
+        const double h = 0.5 * P.comp * dLdc;
+        Gm[0] += h * (c0 / P.det0 - P.c / P.det);
+        Gm[3] += h * (a0 / P.det0 - P.a / P.det);
+        Gm[1] += h * (-P.b / P.det0 + P.b / P.det);
+        Gm[2] += h * (-P.b / P.det0 + P.b / P.det);
+    }
 
     /* Sigma' = T2 Sigma T2^T + eps I:  dL/dSigma = T2^T Gm T2,  dL/dT2 = 2 Gm T2 Sigma */
     double dSig[9], dT2[6], GT[6];

@@ -123,3 +123,13 @@ def test_fd_deep_stack_division_path():
                                       dc=tuple(rng.uniform(0.1, 0.9, 3))))
     g = np.concatenate(rows)
     _fd_check(g, U.identity_cam(32, 32, 30.0), oracle.consts(sh_degree=0), bg=(0.5, 0.5, 0.5), seed=8)
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_fd_mip_2d_filter(seed):
+    """Mip-Splatting's 2D filter (backbone variant): the opacity compensation
+    sqrt(det(S2) / det(S2 + s I)) is differentiated through the covariance;
+    smaller Gaussians (log-scale -3.2) so that the compensation is far from 1."""
+    g, cam = _tiny_scene(6, seed)
+    g[:, 3:6] = np.random.default_rng(seed).normal(-3.2, 0.3, size=(6, 3))
+    _fd_check(g, cam, oracle.consts(sh_degree=1, mip2d=0.1), seed=seed)

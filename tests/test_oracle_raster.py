@@ -373,3 +373,50 @@ def test_adam_matches_torch():
         tp.grad = torch.tensor(gr)
         opt.step()
         np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_sparse_adam_matches_torch_sparse_adam():
+    """The oracle's sparse Adam (planar [59][P], visibility mask) equals
+    torch.optim.SparseAdam on the transposed [P][59] parameter with sparse
+    gradients holding only the visible Gaussians' rows."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(7)
+    P = 50
+    p = rng.normal(size=(59, P))
+    m = np.zeros((59, P)); v = np.zeros((59, P))
+    tp = torch.tensor(p.T.copy(), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.SparseAdam([tp], lr=0.01, betas=(0.9, 0.999), eps=1e-15)
+    for step in range(1, 7):
+        vis = rng.random(P) < 0.6
+        gr = rng.normal(size=(59, P)) * vis[None, :]
+        before = p.copy()
+        oracle.sparse_adam(p, gr, m, v, 0.01, 0.9, 0.999, 1e-15, step, vis)
+        np.testing.assert_array_equal(p[:, ~vis], before[:, ~vis])  # invisible columns untouched
+        idx = np.flatnonzero(vis)
+        tp.grad = torch.sparse_coo_tensor(torch.tensor(idx[None, :]), torch.tensor(gr.T[idx]), size=(P, 59))
+        opt.step()
+        # torch folds the bias corrections into the step size (different rounding order)
+        np.testing.assert_allclose(p, tp.detach().numpy().T, rtol=1e-10, atol=1e-13)
+
+
+def test_mip_2d_filter_isotropic_closed_form():
+    """Mip-Splatting's 2D filter on a single isotropic Gaussian on the optical
+    axis: covariance (f sigma / z)^2 + s in place of the dilation, opacity
+    scaled by (f sigma / z)^2 / ((f sigma / z)^2 + s) (the determinant ratio of
+    2x2 isotropic matrices, square-rooted); the centre pixel gets that alpha."""
+    W = H = 64
+    f, z, o, sigma, s = 60.0, 4.0, 0.7, 0.02, 0.1
+    cam = U.identity_cam(W, H, f, cx=32.5, cy=32.5)
+    g = U.single_gaussian((0, 0, z), [math.log(sigma)] * 3, opacity=o, dc=(0.8, 0.3, 0.55))
+    k = oracle.consts(mip2d=s)
+    out = oracle.forward(g, U.oracle_cam(oracle, cam), k)
+    v0 = (f * sigma / z) ** 2
+    feat = out["proj"]["feat"][0]
+    np.testing.assert_allclose(feat[2:5], [1.0 / (v0 + s), 0.0, 1.0 / (v0 + s)], rtol=1e-12, atol=1e-15)
+    o_eff = o * v0 / (v0 + s)
+    assert feat[5] == pytest.approx(o_eff, rel=1e-12)
+    assert out["proj"]["radius"][0] == math.ceil(3 * math.sqrt(v0 + s))
+    assert out["img"][0, 32, 32] == pytest.approx(o_eff * 0.8, rel=1e-12)
+    # without the filter the same Gaussian keeps its opacity (dilation only)
+    out0 = oracle.forward(g, U.oracle_cam(oracle, cam), oracle.consts())
+    assert out0["proj"]["feat"][0][5] == pytest.approx(o, rel=1e-14)
