@@ -93,7 +93,12 @@ typedef struct dg_camera {
  * result beyond float rounding order.  record: format of the records the
  * render calls read: 0 = the float32 records of dg_project, 1 = the
  * mixed-precision records of dg_pack_records (float16 conic and opacity,
- * bfloat16 colour; transmittance, colour sums and gradients stay float32). */
+ * bfloat16 colour; transmittance, colour sums and gradients stay float32).
+ * mip2d: 0 = the eps2d dilation; > 0 = Mip-Splatting's 2D filter (a backbone
+ * variant of the supplementary): the 2D covariance gets + mip2d I instead of
+ * + eps2d I and the opacity of the record is scaled by
+ * sqrt(det(S2) / det(S2 + mip2d I)) (0 when det(S2) <= 0); dg_project_bwd
+ * differentiates the factor. */
 typedef struct dg_raster_opts {
     int32_t tile;
     int32_t sh_degree;
@@ -103,6 +108,7 @@ typedef struct dg_raster_opts {
     int32_t pixels_per_thread;
     int32_t split_len;
     int32_t record;
+    float mip2d;
 } dg_raster_opts;
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
@@ -304,6 +310,20 @@ DG_API dg_status dg_loss_l1_noalloc(const float* img, const float* target, int64
 DG_API dg_status dg_adam_step(float* params, const float* grads, float* m, float* v, int64_t stride,
                        int64_t P, const float* lr, float beta1, float beta2, float eps,
                        int64_t step, dg_stream stream);
+
+/* Sparse Adam of the Taming-3DGS backbone (supplementary, "Equipping
+ * DashGaussian to Backbones"): the Adam update of dg_adam_step applied only to
+ * the Gaussians whose visible[i] != 0; the others keep their parameters and
+ * their moments (no decay).  The bias corrections use the global step.
+ * visible: device uint8 [P], e.g. from dg_visibility. */
+DG_API dg_status dg_sparse_adam_step(float* params, const float* grads, float* m, float* v, int64_t stride,
+                                     int64_t P, const float* lr, float beta1, float beta2, float eps,
+                                     int64_t step, const uint8_t* visible, dg_stream stream);
+
+/* visible[i] = 1 if Gaussian i has a non-zero radius in any of the n_views
+ * views of a dg_project call (radius: [n_views][P] int32), else 0. */
+DG_API dg_status dg_visibility(const int32_t* radius, int64_t P, int32_t n_views, uint8_t* visible,
+                               dg_stream stream);
 
 /* Adam hyper-parameters of one step, in the layout the kernels read: per-row
  * learning rates, betas, bias corrections bc1 = 1 - beta1^step and

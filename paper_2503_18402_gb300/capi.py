@@ -26,7 +26,8 @@ MAX_VIEWS = 16
 EXPORTS = ("dg_last_error", "dg_abi_version", "dg_kernel_launches", "dg_project", "dg_bin_workspace_size", "dg_bin_count",
            "dg_bin_sort", "dg_render_workspace_size", "dg_render_fwd", "dg_render_bwd", "dg_pack_records", "dg_project_bwd", "dg_project_bwd_adam",
            "dg_loss_workspace_size", "dg_ssim_workspace_size", "dg_loss_l1_dssim",
-           "dg_loss_l1", "dg_loss_l1_noalloc", "dg_adam_step", "dg_adam_hparams_fill", "dg_adam_step_dev", "dg_spectrum_workspace_size",
+           "dg_loss_l1", "dg_loss_l1_noalloc", "dg_adam_step", "dg_adam_hparams_fill", "dg_adam_step_dev",
+           "dg_sparse_adam_step", "dg_visibility", "dg_spectrum_workspace_size",
            "dg_spectrum_accumulate", "dg_spectrum_finalize", "dg_downsample_area", "dg_schedule_init",
            "dg_schedule_step", "dg_schedule_densify", "dg_densify_stats", "dg_densify_workspace_size",
            "dg_densify_mark", "dg_densify_apply", "dg_mse", "dg_opacity_reset")
@@ -48,7 +49,7 @@ class Camera(ctypes.Structure):
 class RasterOpts(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("near_plane", ctypes.c_float),
                 ("eps2d", ctypes.c_float), ("bg", ctypes.c_float * 3), ("pixels_per_thread", ctypes.c_int32),
-                ("split_len", ctypes.c_int32), ("record", ctypes.c_int32)]
+                ("split_len", ctypes.c_int32), ("record", ctypes.c_int32), ("mip2d", ctypes.c_float)]
 
 
 SCHED_MAX_LEVELS = 64
@@ -99,13 +100,14 @@ def camera(viewmat, fx, fy, cx, cy, width, height) -> Camera:
 
 
 def raster_opts(tile=16, sh_degree=3, near_plane=0.2, eps2d=0.3, bg=(0.0, 0.0, 0.0),
-                pixels_per_thread=0, split_len=0, record=0) -> RasterOpts:
+                pixels_per_thread=0, split_len=0, record=0, mip2d=0.0) -> RasterOpts:
     o = RasterOpts()
     o.tile, o.sh_degree, o.near_plane, o.eps2d = int(tile), int(sh_degree), float(near_plane), float(eps2d)
     o.bg[:] = [float(b) for b in bg]
     o.pixels_per_thread = int(pixels_per_thread)
     o.split_len = int(split_len)
     o.record = int(record)
+    o.mip2d = float(mip2d)
     return o
 
 
@@ -139,6 +141,9 @@ _SIGS = {
     "dg_loss_l1": ([_P, _P, _I64, _P, _P, _P, _SZ, _P], _ST),
     "dg_loss_l1_noalloc": ([_P, _P, _I64, _P, _P, _P], _ST),
     "dg_adam_step": ([_P, _P, _P, _P, _I64, _I64, _P, _F, _F, _F, _I64, _P], _ST),
+    "dg_sparse_adam_step": ([_P, _P, _P, _P, _I64, _I64, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I64,
+                             _P, _P], _ST),
+    "dg_visibility": ([_P, _I64, _I32, _P, _P], _ST),
     "dg_adam_hparams_fill": ([_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I64, _P], _ST),
     "dg_adam_step_dev": ([_P, _P, _P, _P, _I64, _I64, _P, _P, _P], _ST),
     "dg_spectrum_workspace_size": ([_I32, _I32], _SZ),
@@ -298,6 +303,17 @@ def dg_loss_l1_dssim(img, target, sizes, lam, dL_dimg, loss, ws, ws_bytes, strea
 def dg_loss_l1_noalloc(img, target, n, dL_dimg, loss, stream=None):
     """dg_loss_l1 without a workspace: for callers that cannot allocate device memory."""
     _check(_lib.dg_loss_l1_noalloc(_a(img), _a(target), n, _a(dL_dimg), _a(loss), _s(stream)))
+
+
+def dg_sparse_adam_step(params, grads, m, v, stride, P, lr, beta1, beta2, eps, step, visible, stream=None):
+    lr_arr = (ctypes.c_float * NPARAM)(*[float(x) for x in lr])
+    _check(_lib.dg_sparse_adam_step(_a(params), _a(grads), _a(m), _a(v), stride, P,
+                                    ctypes.cast(lr_arr, ctypes.c_void_p), beta1, beta2, eps, step, _a(visible),
+                                    _s(stream)))
+
+
+def dg_visibility(radius, P, n_views, visible, stream=None):
+    _check(_lib.dg_visibility(_a(radius), P, n_views, _a(visible), _s(stream)))
 
 
 class AdamHparams(ctypes.Structure):

@@ -88,7 +88,7 @@ __global__ void k_opacity_reset(float* __restrict__ prm, float* __restrict__ m, 
 __global__ void __launch_bounds__(256)
 k_adam(float* __restrict__ prm, const float* __restrict__ grd, float* __restrict__ m,
        float* __restrict__ v, long long stride, long long P, AdamHp hp_val, const AdamHp* __restrict__ hp_dev,
-       const int* __restrict__ skip_if)
+       const int* __restrict__ skip_if, const uint8_t* __restrict__ vis)
 {
     const int row = blockIdx.y;
     const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
@@ -100,17 +100,25 @@ k_adam(float* __restrict__ prm, const float* __restrict__ grd, float* __restrict
     const bool vec = ((o & 3) == 0) && (i0 + 3 < P) && ((((uintptr_t)prm) & 15u) == 0) &&
                      ((((uintptr_t)grd) & 15u) == 0) && ((((uintptr_t)m) & 15u) == 0) &&
                      ((((uintptr_t)v) & 15u) == 0);
+    // sparse Adam: Gaussians outside the visibility mask keep parameters and moments
+    uint8_t on[4] = {1, 1, 1, 1};
+    if (vis) {
+        for (int c = 0; c < 4; ++c) on[c] = i0 + c < P ? vis[i0 + c] : 0;
+        if (!(on[0] | on[1] | on[2] | on[3])) return;
+    }
     if (vec) {
         float4 p = *(float4*)(prm + o), g = *(const float4*)(grd + o);
         float4 mm = *(float4*)(m + o), vv = *(float4*)(v + o);
         float* pp = &p.x; const float* gg = &g.x; float* mp = &mm.x; float* vp = &vv.x;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) adam_update(pp[c], mp[c], vp[c], gg[c], lr, hp);
+        for (int c = 0; c < 4; ++c)
+            if (on[c]) adam_update(pp[c], mp[c], vp[c], gg[c], lr, hp);
         *(float4*)(prm + o) = p;
         *(float4*)(m + o) = mm;
         *(float4*)(v + o) = vv;
     } else {
         for (int c = 0; c < 4 && i0 + c < P; ++c) {
+            if (!on[c]) continue;
             const long long k = o + c;
             float pc = prm[k], mc = m[k], vc = v[k];
             adam_update(pc, mc, vc, grd[k], lr, hp);
@@ -152,7 +160,8 @@ extern "C" dg_status dg_adam_step_dev(float* params, const float* grads, float* 
     if (!params || !grads || !m || !v || !hp_dev) { dg_set_error("null buffer"); return DG_ERR_ARG; }
     const long long per = 256 * 4;
     dim3 grid((unsigned)((P + per - 1) / per), DG_NPARAM);
-    dg::k_adam<<<grid, 256, 0, (cudaStream_t)stream>>>(params, grads, m, v, stride, P, dg::AdamHp{}, hp_dev, skip_if);
+    dg::k_adam<<<grid, 256, 0, (cudaStream_t)stream>>>(params, grads, m, v, stride, P, dg::AdamHp{}, hp_dev, skip_if,
+                                                        nullptr);
     dg_note_launch();
     return dg_check_launch("adam_dev");
 }
@@ -190,9 +199,46 @@ extern "C" dg_status dg_adam_step(float* params, const float* grads, float* m, f
     const dg::AdamHp hp = dg_adam_hp(lr, beta1, beta2, eps, step);
     const long long per = 256 * 4;
     dim3 grid((unsigned)((P + per - 1) / per), DG_NPARAM);
-    dg::k_adam<<<grid, 256, 0, (cudaStream_t)stream>>>(params, grads, m, v, stride, P, hp, nullptr, nullptr);
+    dg::k_adam<<<grid, 256, 0, (cudaStream_t)stream>>>(params, grads, m, v, stride, P, hp, nullptr, nullptr, nullptr);
     dg_note_launch();
     return dg_check_launch("adam");
+}
+
+namespace dg {
+__global__ void k_visibility(const int* __restrict__ radius, long long P, int n_views, uint8_t* __restrict__ vis)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    uint8_t on = 0;
+    for (int v = 0; v < n_views; ++v) on |= radius[(long long)v * P + i] > 0;
+    vis[i] = on;
+}
+}  // namespace dg
+
+extern "C" dg_status dg_visibility(const int32_t* radius, int64_t P, int32_t n_views, uint8_t* visible,
+                                   dg_stream stream)
+{
+    if (P < 0 || n_views < 1 || n_views > DG_MAX_VIEWS) { dg_set_error("bad P/n_views"); return DG_ERR_ARG; }
+    if (P == 0) return DG_OK;
+    if (!radius || !visible) { dg_set_error("null buffer"); return DG_ERR_ARG; }
+    dg::k_visibility<<<(unsigned)((P + 255) / 256), 256, 0, (cudaStream_t)stream>>>(radius, P, n_views, visible);
+    dg_note_launch();
+    return dg_check_launch("visibility");
+}
+
+extern "C" dg_status dg_sparse_adam_step(float* params, const float* grads, float* m, float* v, int64_t stride,
+                                         int64_t P, const float* lr, float beta1, float beta2, float eps,
+                                         int64_t step, const uint8_t* visible, dg_stream stream)
+{
+    if (P < 0 || stride < P || step < 1) { dg_set_error("bad P/stride/step"); return DG_ERR_ARG; }
+    if (P == 0) return DG_OK;
+    if (!params || !grads || !m || !v || !lr || !visible) { dg_set_error("null buffer"); return DG_ERR_ARG; }
+    const dg::AdamHp hp = dg_adam_hp(lr, beta1, beta2, eps, step);
+    const long long per = 256 * 4;
+    dim3 grid((unsigned)((P + per - 1) / per), DG_NPARAM);
+    dg::k_adam<<<grid, 256, 0, (cudaStream_t)stream>>>(params, grads, m, v, stride, P, hp, nullptr, nullptr, visible);
+    dg_note_launch();
+    return dg_check_launch("sparse_adam");
 }
 
 extern "C" dg_status dg_mse(const float* a, const float* b, int64_t n, float* mse, void* ws, size_t ws_bytes,

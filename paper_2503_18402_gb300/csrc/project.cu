@@ -121,11 +121,14 @@ struct Splat {
     bool gx, gy;            // frustum guard active on x / y
     float lx, ly;           // signed guard value when active
     float t2[6];            // J R, 2 x 3
-    float a, b, c, det;     // 2D covariance (with dilation) and determinant
+    float a, b, c, det;     // 2D covariance (with dilation or 2D filter) and determinant
     float A, B, C;          // conic
+    float det0, comp;       // 2D filter: undilated determinant, opacity factor sqrt(det0 / det)
 };
 
-__device__ inline bool splat(const G3& g, const Cam& cam, float near_plane, float eps2d, Splat& S)
+// mip2d > 0: Mip-Splatting's 2D filter, S2 + mip2d I in place of the dilation,
+// with the opacity scaled by sqrt(det(S2) / det(S2 + mip2d I)); else the eps2d dilation.
+__device__ inline bool splat(const G3& g, const Cam& cam, float near_plane, float eps2d, float mip2d, Splat& S)
 {
     S.t[0] = cam.r[0] * g.p[0] + cam.r[1] * g.p[1] + cam.r[2] * g.p[2] + cam.t[0];
     S.t[1] = cam.r[3] * g.p[0] + cam.r[4] * g.p[1] + cam.r[5] * g.p[2] + cam.t[1];
@@ -159,11 +162,20 @@ __device__ inline bool splat(const G3& g, const Cam& cam, float near_plane, floa
         u[1] = sg[1] * tr[0] + sg[3] * tr[1] + sg[4] * tr[2];
         u[2] = sg[2] * tr[0] + sg[4] * tr[1] + sg[5] * tr[2];
     }
-    S.a = S.t2[0] * u0[0] + S.t2[1] * u0[1] + S.t2[2] * u0[2] + eps2d;
+    const float a0 = S.t2[0] * u0[0] + S.t2[1] * u0[1] + S.t2[2] * u0[2];
     S.b = S.t2[0] * u1[0] + S.t2[1] * u1[1] + S.t2[2] * u1[2];
-    S.c = S.t2[3] * u1[0] + S.t2[4] * u1[1] + S.t2[5] * u1[2] + eps2d;
+    const float c0 = S.t2[3] * u1[0] + S.t2[4] * u1[1] + S.t2[5] * u1[2];
+    const float dil = mip2d > 0.f ? mip2d : eps2d;
+    S.a = a0 + dil;
+    S.c = c0 + dil;
     S.det = fmaf(S.a, S.c, -S.b * S.b);
     if (!(S.det > 0.f)) return false;
+    S.comp = 1.f;
+    S.det0 = 0.f;
+    if (mip2d > 0.f) {
+        S.det0 = fmaf(a0, c0, -S.b * S.b);
+        S.comp = S.det0 > 0.f ? sqrtf(S.det0 / S.det) : 0.f;
+    }
     const float inv = 1.f / S.det;
     S.A = S.c * inv;
     S.B = -S.b * inv;
@@ -202,7 +214,7 @@ __device__ inline const ViewSet& block_views(const ViewSet& vs, const dg_camera*
 template <int NB>
 __global__ void __launch_bounds__(128)
 k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs_host, const dg_camera* cdev, int B,
-              float near_plane, float eps2d, float4* __restrict__ feat, float* __restrict__ depth,
+              float near_plane, float eps2d, float mip2d, float4* __restrict__ feat, float* __restrict__ depth,
               int* __restrict__ radius, int* __restrict__ tiles, uint8_t* __restrict__ clampm)
 {
     __shared__ ViewSet s_vs;
@@ -216,7 +228,7 @@ k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs
     for (int k = 0; k < NB; ++k)
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) sh[k][ch] = prm[(11 + 3 * k + ch) * stride + i];
-    const float o = 1.f / (1.f + expf(-prm[10 * stride + i]));
+    const float osig = 1.f / (1.f + expf(-prm[10 * stride + i]));
     for (int v = 0; v < vs.n; ++v) {
         const Cam& cam = vs.cam[v];
         const size_t r = (size_t)v * P + i;
@@ -224,7 +236,7 @@ k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs
         float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f), f1 = f0, f2 = f0;
         int rad = 0, nt = 0;
         uint8_t cm = 0;
-        const bool ok = splat(g, cam, near_plane, eps2d, S);
+        const bool ok = splat(g, cam, near_plane, eps2d, mip2d, S);
         if (ok) {
             const float tz = S.t[2];
             const float lam = 0.5f * (S.a + S.c) + sqrtf(0.25f * (S.a - S.c) * (S.a - S.c) + S.b * S.b);
@@ -253,7 +265,7 @@ k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs
                     rad = rr;
                     nt = (q.x1 - q.x0) * (q.y1 - q.y0);
                     f0 = make_float4(u, vv, S.A, S.B);
-                    f1 = make_float4(S.C, o, col[0], col[1]);
+                    f1 = make_float4(S.C, osig * S.comp, col[0], col[1]);
                     f2 = make_float4(col[2], 0.f, 0.f, 0.f);
                 }
             }
@@ -279,7 +291,7 @@ k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs
 template <int NB, bool ADAM, bool SINGLE>
 __global__ void __launch_bounds__(128, 4)
 k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host, const dg_camera* cdev,
-              float near_plane, float eps2d, const int* __restrict__ radius, const uint8_t* __restrict__ clampm,
+              float near_plane, float eps2d, float mip2d, const int* __restrict__ radius, const uint8_t* __restrict__ clampm,
               const float4* __restrict__ grad2d, float* __restrict__ grads, float* __restrict__ am,
               float* __restrict__ av, AdamHp hp)
 {
@@ -300,6 +312,7 @@ k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host,
     };
     G3 g;
     gauss3d(prm, stride, i, g);
+    const float osig = 1.f / (1.f + expf(-prm[10 * stride + i]));
     float dp[3] = {0.f, 0.f, 0.f};
     float dsg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma (xx xy xz yy yz zz), off-diagonals counted once
     float dop = 0.f;
@@ -315,11 +328,11 @@ k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host,
         if (radius[r] == 0) continue;
         const Cam& cam = vs.cam[v];
         Splat S;
-        if (!splat(g, cam, near_plane, eps2d, S)) continue;
+        if (!splat(g, cam, near_plane, eps2d, mip2d, S)) continue;
         any = true;
         const float4 g0 = grad2d[3 * r], g1 = grad2d[3 * r + 1], g2 = grad2d[3 * r + 2];
         const float dLu = g0.x, dLv = g0.y, dLA = g0.z, dLB = g0.w, dLC = g1.x;
-        dop += g1.y;
+        dop += g1.y * S.comp;  // record opacity = sigmoid * comp
         const uint8_t cm = clampm[r];
         const float dcol[3] = {(cm & 1u) ? 0.f : g1.z, (cm & 2u) ? 0.f : g1.w, (cm & 4u) ? 0.f : g2.x};
         // colour: SH coefficients and the view direction
@@ -358,9 +371,20 @@ k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host,
         const float A = S.A, B = S.B, C = S.C;
         const float k00 = A * dLA + 0.5f * B * dLB, k01 = 0.5f * A * dLB + B * dLC;
         const float k10 = B * dLA + 0.5f * C * dLB, k11 = 0.5f * B * dLB + C * dLC;
-        const float gm00 = -(k00 * A + k01 * B);
-        const float gm01 = -(k00 * B + k01 * C);
-        const float gm11 = -(k10 * B + k11 * C);
+        float gm00 = -(k00 * A + k01 * B);
+        float gm01 = -(k00 * B + k01 * C);
+        float gm11 = -(k10 * B + k11 * C);
+        if (mip2d > 0.f && S.det0 > 0.f) {
+            // 2D filter: d sqrt(det0 / det) per covariance entry (det0 of the
+            // undilated, det of the filtered matrix; the off-diagonal entry
+            // carries half of the derivative in b)
+            const float h = 0.5f * S.comp * g1.y * osig;
+            const float a0 = S.a - mip2d, c0 = S.c - mip2d;
+            const float i0 = 1.f / S.det0, i1 = 1.f / S.det;
+            gm00 += h * (c0 * i0 - S.c * i1);
+            gm11 += h * (a0 * i0 - S.a * i1);
+            gm01 += h * (S.b * i1 - S.b * i0);
+        }
         // Sigma2 = T2 Sigma T2^T:  dSigma = T2^T Gm T2,  dT2 = 2 Gm T2 Sigma
         const float* t2 = S.t2;
         float gt[6];  // Gm T2
@@ -414,10 +438,7 @@ k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host,
     put(0, dp[0]);
     put(1, dp[1]);
     put(2, dp[2]);
-    {
-        const float o = 1.f / (1.f + expf(-prm[10 * stride + i]));
-        put(10, dop * o * (1.f - o));
-    }
+    put(10, dop * osig * (1.f - osig));
 #pragma unroll
     for (int k = SINGLE ? NB : 0; k < 16; ++k)
 #pragma unroll
@@ -467,6 +488,7 @@ static bool check_opts(const dg_raster_opts* o)
     if (!o) { dg_set_error("opts is null"); return false; }
     if (o->tile < 1 || o->tile > 64) { dg_set_error("tile %d outside 1..64", o->tile); return false; }
     if (o->sh_degree < 0 || o->sh_degree > 3) { dg_set_error("sh_degree %d outside 0..3", o->sh_degree); return false; }
+    if (!(o->mip2d >= 0.f)) { dg_set_error("mip2d must be >= 0"); return false; }
     return true;
 }
 
@@ -501,10 +523,10 @@ extern "C" dg_status dg_project(const float* params, int64_t stride, int64_t P, 
     const int blocks = (int)((P + threads - 1) / threads);
     cudaStream_t s = (cudaStream_t)stream;
     switch (opts->sh_degree) {
-    case 0: dg::k_project_fwd<1><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, (float4*)feat, depth, radius, tiles, clamp); break;
-    case 1: dg::k_project_fwd<4><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, (float4*)feat, depth, radius, tiles, clamp); break;
-    case 2: dg::k_project_fwd<9><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, (float4*)feat, depth, radius, tiles, clamp); break;
-    default: dg::k_project_fwd<16><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, (float4*)feat, depth, radius, tiles, clamp); break;
+    case 0: dg::k_project_fwd<1><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, opts->mip2d, (float4*)feat, depth, radius, tiles, clamp); break;
+    case 1: dg::k_project_fwd<4><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, opts->mip2d, (float4*)feat, depth, radius, tiles, clamp); break;
+    case 2: dg::k_project_fwd<9><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, opts->mip2d, (float4*)feat, depth, radius, tiles, clamp); break;
+    default: dg::k_project_fwd<16><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, opts->mip2d, (float4*)feat, depth, radius, tiles, clamp); break;
     }
     dg_note_launch();
     return dg_check_launch("project_fwd");
@@ -516,12 +538,12 @@ static void launch_project_bwd(int nb, int blocks, int threads, cudaStream_t s, 
                                const int32_t* radius, const uint8_t* clamp, const float4* g2, float* grads, float* m,
                                float* v, const dg::AdamHp& hp)
 {
-    const float np = opts->near_plane, e2 = opts->eps2d;
+    const float np = opts->near_plane, e2 = opts->eps2d, mp = opts->mip2d;
     switch (nb) {
-    case 1: dg::k_project_bwd<1, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, radius, clamp, g2, grads, m, v, hp); break;
-    case 4: dg::k_project_bwd<4, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, radius, clamp, g2, grads, m, v, hp); break;
-    case 9: dg::k_project_bwd<9, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, radius, clamp, g2, grads, m, v, hp); break;
-    default: dg::k_project_bwd<16, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, radius, clamp, g2, grads, m, v, hp); break;
+    case 1: dg::k_project_bwd<1, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, mp, radius, clamp, g2, grads, m, v, hp); break;
+    case 4: dg::k_project_bwd<4, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, mp, radius, clamp, g2, grads, m, v, hp); break;
+    case 9: dg::k_project_bwd<9, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, mp, radius, clamp, g2, grads, m, v, hp); break;
+    default: dg::k_project_bwd<16, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, mp, radius, clamp, g2, grads, m, v, hp); break;
     }
 }
 

@@ -83,6 +83,11 @@ class TrainConfig:
     # records read by the render passes: 0 float32, 1 mixed (float16 conic and
     # opacity, bfloat16 colour; float32 transmittance, sums and gradients)
     record: int = 0
+    # Sparse Adam (the Taming-3DGS backbone's optimiser): only Gaussians visible
+    # in the step's views are updated
+    sparse_adam: bool = False
+    # Mip-Splatting's 2D filter in place of the dilation (backbone variant); 0 = off
+    mip2d: float = 0.0
     # projection adjoint fused with the Adam update (no stored gradient); off:
     # the fused kernel's register footprint (one thread per Gaussian holding all
     # 59 gradients) leaves too few warps resident to stream params, m and v
@@ -111,7 +116,7 @@ class Trainer:
         self.acc = torch.zeros(cap, **f32)
         self.den = torch.zeros(cap, **f32)
         self.maxr = torch.zeros(cap, **f32)
-        self.tuner = RenderTuner(self.dev, capi.raster_opts(record=cfg.record),
+        self.tuner = RenderTuner(self.dev, capi.raster_opts(record=cfg.record, mip2d=cfg.mip2d),
                                  fixed=None if cfg.autotune else Shape(16, 2, 4, 0))
         self.rz = self.tuner.rasterizer(Shape(8, 1, 1, 0))  # evaluation renders
         n_full = 3 * self.H * self.W
@@ -225,8 +230,7 @@ class Trainer:
                 capi.dg_densify_stats(rz.grad2d, rz.radius, P, cams, V, self.acc, self.den, self.maxr, self.stream)
             capi.dg_project_bwd(params, self.cap, P, cams, V, rz.opts, rz.radius, rz.clamp, rz.grad2d,
                                 self.grads[:, :P], self.stream)
-            capi.dg_adam_step(b["p"], self.grads, b["m"], b["v"], self.cap, P, lr, 0.9, 0.999, 1e-15, k + 1,
-                              self.stream)
+            self._adam(b, P, lr, k, rz.radius, V)
             return r, fr.M
         # graph path: one graph per (P, size, stats window, buffer set); the
         # status of a step is read two steps later, so the host prepares the
@@ -245,7 +249,8 @@ class Trainer:
                 fr0 = rz0.forward(b["p"][:, :P], P, cams, self.stream)
                 hint = fr0.M
             M_cap = int(hint * 1.5) + 4096
-            g = StepGraph(self.dev, capi.raster_opts(tile=8, record=cfg.record), 1, 1, b["p"], b["m"], b["v"],
+            g = StepGraph(self.dev, capi.raster_opts(tile=8, record=cfg.record, mip2d=cfg.mip2d), 1, 1, b["p"],
+                          b["m"], b["v"],
                           self.grads, self.cap, P,
                           cams, M_cap, cfg.ssim_lambda, (self.acc, self.den, self.maxr) if stats_on else None)
             g.key = key
@@ -268,6 +273,17 @@ class Trainer:
             if status != 0:  # pair capacity exceeded: that step made no update
                 self.skipped_steps += 1
                 self.graphs.pop(g_prev.key, None)
+
+    def _adam(self, b, P, lr, k, radius, V):
+        if self.cfg.sparse_adam:
+            if getattr(self, "vis", None) is None or self.vis.numel() < self.cap:
+                self.vis = torch.zeros(self.cap, dtype=torch.uint8, device=self.dev)
+            capi.dg_visibility(radius, P, V, self.vis, self.stream)
+            capi.dg_sparse_adam_step(b["p"], self.grads, b["m"], b["v"], self.cap, P, lr, 0.9, 0.999, 1e-15, k + 1,
+                                     self.vis, self.stream)
+        else:
+            capi.dg_adam_step(b["p"], self.grads, b["m"], b["v"], self.cap, P, lr, 0.9, 0.999, 1e-15, k + 1,
+                              self.stream)
 
     def dL_b(self, n):
         if getattr(self, "_dLb", None) is None or self._dLb.numel() < n:
@@ -323,13 +339,12 @@ class Trainer:
             capi.dg_densify_stats(rz.grad2d, rz.radius, P, cam, 1, self.acc, self.den, self.maxr, self.stream)
         lr = [lr_pos] * 3 + [cfg.lr_scale] * 3 + [cfg.lr_rot] * 4 + [cfg.lr_opacity] + [cfg.lr_dc] * 3 + \
              [cfg.lr_rest] * 45
-        if cfg.fused_adam:
+        if cfg.fused_adam and not cfg.sparse_adam:
             rz.project_bwd_adam(b["p"], self.cap, fr, b["m"], b["v"], lr, k + 1, stream=self.stream)
         else:
             capi.dg_project_bwd(params, self.cap, P, cam, 1, rz.opts, rz.radius, rz.clamp, rz.grad2d,
                                 self.grads[:, :P], self.stream)
-            capi.dg_adam_step(b["p"], self.grads, b["m"], b["v"], self.cap, P, lr, 0.9, 0.999, 1e-15, k + 1,
-                              self.stream)
+            self._adam(b, P, lr, k, rz.radius, 1)
         return r, fr.M
 
     def densify(self, k):
@@ -435,6 +450,8 @@ def main(argv=None):
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--views-per-step", type=int, default=1)
     ap.add_argument("--cuda-graph", action="store_true", help="capture each step in a CUDA graph")
+    ap.add_argument("--sparse-adam", action="store_true", help="update only visible Gaussians (Taming-3DGS)")
+    ap.add_argument("--mip2d", type=float, default=0.0, help="Mip-Splatting 2D filter variance (0: dilation)")
     ap.add_argument("--record", choices=["fp32", "mixed"], default="fp32",
                     help="render-side record storage (mixed: float16 conic/opacity, bfloat16 colour)")
     args = ap.parse_args(argv)
@@ -449,7 +466,8 @@ def main(argv=None):
                           reso_sched=arm in ("scheduled", "reso"), prim_sched=arm in ("scheduled", "prim"),
                           a=args.a, gamma=args.gamma, ssim_lambda=args.ssim_lambda, autotune=not args.no_autotune,
                           views_per_step=args.views_per_step, cuda_graph=args.cuda_graph,
-                          record=1 if args.record == "mixed" else 0)
+                          record=1 if args.record == "mixed" else 0, sparse_adam=args.sparse_adam,
+                          mip2d=args.mip2d)
         if args.iters < 30000:  # compress the backbone's iteration windows proportionally
             s = args.iters / 30000
             cfg.densify_from = max(1, int(500 * s)); cfg.densify_until = int(15000 * s)

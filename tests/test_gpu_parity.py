@@ -612,3 +612,73 @@ def test_batched_views_match_single_view_renders():
         assert np.abs(G.np_(frb.Ts[v]) - orf["T"]).max() <= 1e-5
         np.testing.assert_array_equal(G.np_(frb.lasts[v]), orf["last"])
         np.testing.assert_array_equal(G.np_(rzb.blended[v]), orf["blended"])
+
+
+def test_sparse_adam_parity():
+    rng = np.random.default_rng(9)
+    P, stride = 1003, 1010
+    p = rng.normal(size=(59, stride)).astype(np.float32)
+    lr = np.linspace(1e-4, 1e-2, 59).astype(np.float32)
+    radius = np.where(rng.random((2, P)) < 0.4, rng.integers(1, 9, size=(2, P)), 0).astype(np.int32)
+    vis_ref = (radius > 0).any(axis=0)
+    vis = torch.zeros(P, dtype=torch.uint8, device="cuda")
+    capi.dg_visibility(torch.from_numpy(radius.reshape(-1)).cuda(), P, 2, vis)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(G.np_(vis).astype(bool), vis_ref)
+    tp = torch.from_numpy(p.copy()).cuda()
+    m = torch.zeros_like(tp); v = torch.zeros_like(tp)
+    op = p[:, :P].astype(np.float64).copy(); om = np.zeros_like(op); ov = np.zeros_like(op)
+    for step in range(1, 5):
+        gr = rng.normal(size=(59, stride)).astype(np.float32)
+        capi.dg_sparse_adam_step(tp, torch.from_numpy(gr).cuda(), m, v, stride, P, lr, 0.9, 0.999, 1e-15, step, vis)
+        oracle.sparse_adam(op, gr[:, :P].astype(np.float64), om, ov, lr[:, None].astype(np.float64), 0.9, 0.999,
+                           1e-15, step, vis_ref)
+    torch.cuda.synchronize()
+    got = G.np_(tp)
+    np.testing.assert_allclose(got[:, :P], op, rtol=1e-5, atol=1e-6)
+    np.testing.assert_array_equal(got[:, :P][:, ~vis_ref], p[:, :P][:, ~vis_ref])
+    assert float(G.np_(m)[:, :P][:, ~vis_ref].__abs__().max()) == 0.0
+
+
+def test_mip_2d_filter_matches_oracle():
+    """Mip-Splatting's 2D filter (opts.mip2d): records (conic, compensated
+    opacity), image and full parameter gradient against the FP64 oracle with
+    the same filter."""
+    g = synth.random_gaussians(2000, 88)
+    g[:, 3:6] -= 1.0  # small footprints: compensation factors well below 1
+    cam = synth.camera_cfg0(64, 64, 4.0)
+    bg = (0.1, 0.2, 0.3)
+    opts = capi.raster_opts(mip2d=0.1, bg=bg)
+    k = oracle.consts(mip2d=0.1)
+    rz = Rasterizer("cuda", opts)
+    params = G.gpu_params(g)
+    gcam = G.gpu_camera(cam)
+    fr = rz.forward(params, g.shape[0], gcam, examined=True)
+    torch.cuda.synchronize()
+    rec = _records(rz, g.shape[0])
+    g64, ocam = G.f32(g), G.oracle_camera(cam)
+    pr = oracle.project(g64, ocam, k)
+    vis = pr["radius"] > 0
+    assert vis.sum() > 500
+    np.testing.assert_array_equal(rec["radius"] > 0, vis)
+    f, fo = rec["feat"][vis], pr["feat"][vis]
+    assert fo[:, 5].min() < 0.5 * G.np_(torch.sigmoid(params[10]))[vis].max()  # compensation active
+    cn = np.abs(fo[:, 2:5]).max(axis=1, keepdims=True)
+    assert np.all(np.abs(f[:, 2:5] - fo[:, 2:5]) <= 1e-4 * cn)
+    np.testing.assert_allclose(f[:, 5], fo[:, 5], rtol=1e-5, atol=1e-7)
+    gid, ranges = _gpu_bins(rz, fr)
+    orf = oracle.render_fwd(rec["feat"], 64, 64, 16, gid, ranges, G.f32(bg), k)
+    assert np.abs(G.np_(fr.img) - orf["img"]).max() <= 1e-5
+    np.testing.assert_array_equal(G.np_(fr.last), orf["last"])
+    rng = np.random.default_rng(4)
+    dL = (rng.normal(size=(3, 64, 64)) / (3 * 64 * 64)).astype(np.float32)
+    grads = torch.empty_like(params)
+    rz.backward(params, fr, torch.from_numpy(dL).cuda(), grads)
+    torch.cuda.synchronize()
+    g2 = G.np_(rz.grad2d[: g.shape[0]])[:, :9]
+    og2 = oracle.render_bwd(rec["feat"], 64, 64, 16, gid, ranges, G.f32(bg), k, dL.astype(np.float64))
+    ok, worst, nbad = G.grad_close(g2, og2)
+    assert ok, (worst, nbad)
+    og = oracle.project_bwd(g64, ocam, k, g2.astype(np.float64))
+    ok, worst, nbad = G.grad_close(G.np_(grads).T, og)
+    assert ok, (worst, nbad)
