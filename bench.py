@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--record", choices=["fp32", "mixed"], default="fp32",
                     help="render-side record storage (mixed: float16 conic/opacity, bfloat16 colour)")
+    ap.add_argument("--graph", action="store_true",
+                    help="also time the step captured as one CUDA graph (graph_ms_per_view)")
     ap.add_argument("--fused-adam", action="store_true",
                     help="projection adjoint fused with Adam (default: two kernels)")
     ap.add_argument("--cpu-frac", type=float, default=0.125,
@@ -263,6 +265,39 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         elapsed_ms = float(tt.item())
 
+    # the same step captured once as a CUDA graph and replayed per view (new
+    # camera, Adam hyper-parameters and target written to device buffers)
+    graph_ms = None
+    if args.graph:
+        from paper_2503_18402_gb300.graphstep import StepGraph
+        gshape = shape
+        gr = tuner.rasterizer(gshape)
+        fr0 = gr.forward(params, P, gcams[0])
+        M_cap = int(max(M_tot) * 1.25) + 4096
+        sg = StepGraph(dev, gr.opts, gshape.ppt_fwd, gshape.ppt_bwd, params, m, v, grads, stride, P, [gcams[0]],
+                       M_cap, 0.2)
+        adam_t[0] += 1
+        sg.capture([gcams[0]], capi.dg_adam_hparams_fill(lr, 0.9, 0.999, 1e-15, adam_t[0]), [targets[0]])
+        for i in range(args.warmup):
+            adam_t[0] += 1
+            sg.replay([gcams[i % N_VIEWS]], capi.dg_adam_hparams_fill(lr, 0.9, 0.999, 1e-15, adam_t[0]),
+                      [targets[i % N_VIEWS]])
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        hps = [capi.dg_adam_hparams_fill(lr, 0.9, 0.999, 1e-15, adam_t[0] + 1 + i) for i in range(args.steps)]
+        g0.record(stream)
+        for i in range(args.steps):
+            sg.replay([gcams[i % N_VIEWS]], hps[i], [targets[i % N_VIEWS]])
+        g1.record(stream)
+        torch.cuda.synchronize()
+        adam_t[0] += args.steps
+        graph_ms = g0.elapsed_time(g1) / args.steps
+        status, _ = sg.result()
+        if status != 0:
+            graph_ms = None  # a step exceeded the graph's pair capacity: no valid number
+        del sg
+
     # end to end through the public API: target copied from pinned host memory
     # each step, loss read back each step
     pinned = [t.cpu().pin_memory() for t in targets]
@@ -331,6 +366,8 @@ def run_ours(args):
     out["e2e"] = {"value": round(e2e_ms / views_total, 4), "unit": "ms/view",
                   "h2d_bytes_per_step": int(targets[0].numel() * 4), "d2h_bytes_per_step": 4 + 8}
     out["gpu_launches"] = int(launches)
+    if graph_ms is not None:
+        out["graph_ms_per_view"] = round(graph_ms, 4)
     out["clocks"] = clk
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(model, views[0], frac=args.cpu_frac)

@@ -194,13 +194,17 @@ DG_API dg_status dg_bin_sort(const float* feat, const int32_t* radius, int64_t P
 DG_API dg_status dg_pack_records(const float* feat, int64_t n_records, void* packed, dg_stream stream);
 
 /* ---------------------------------------------------------------------- */
-/* Render workspace for these cameras and options: work counters of the
- * persistent launches and, unless opts->split_len < 0, the split plan and
- * per-pixel chunk state (about 40 MB plus 40 bytes per tile).  Returns 0 for
- * invalid arguments.  The workspace must be 256-byte aligned.  dg_render_bwd
- * must get the workspace, cameras, tile and split_len of the dg_render_fwd
- * of the same batch, unmodified in between. */
-DG_API size_t dg_render_workspace_size(const dg_camera* cams, int32_t n_views, const dg_raster_opts* opts);
+/* Render workspace for these cameras and options and up to M_cap pairs: work
+ * counters of the persistent launches, unless opts->split_len < 0 the split
+ * plan and per-pixel chunk state (about 40 MB plus 40 bytes per tile), and one
+ * byte per pair in which the forward records whether some pixel of the pair's
+ * tile blended it (the backward then stages only those entries; pairs beyond
+ * the bytes a smaller workspace holds fall back to the tile test).  Returns 0
+ * for invalid arguments.  The workspace must be 256-byte aligned.
+ * dg_render_bwd must get the workspace, cameras, tile and split_len of the
+ * dg_render_fwd of the same batch, unmodified in between. */
+DG_API size_t dg_render_workspace_size(const dg_camera* cams, int32_t n_views, const dg_raster_opts* opts,
+                                       int64_t M_cap);
 
 /* Forward compositing, Eq. 1: per pixel, front to back over its tile's list,
  * C = sum_i T_i alpha_i c_i + T_N bg.  One persistent launch covers every

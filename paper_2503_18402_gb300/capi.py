@@ -128,7 +128,7 @@ _SIGS = {
     "dg_bin_workspace_size": ([_I64, _I32, _I64], _SZ),
     "dg_bin_count": ([_P, _P, _I64, _I32, _P, _SZ, _I64, _P, _P], _ST),
     "dg_bin_sort": ([_P, _P, _I64, _CAM, _I32, _I32, _P, _SZ, _I64, _P, _P, _P, _P], _ST),
-    "dg_render_workspace_size": ([_CAM, _I32, _OPT], _SZ),
+    "dg_render_workspace_size": ([_CAM, _I32, _OPT, _I64], _SZ),
     "dg_pack_records": ([_P, _I64, _P, _P], _ST),
     "dg_render_fwd": ([_P, _P, _P, _CAM, _I32, _OPT, _P, _P, _P, _P, _P, _P, _SZ, _P], _ST),
     "dg_render_bwd": ([_P, _P, _P, _CAM, _I32, _OPT, _P, _P, _P, _I64, _P, _P, _SZ, _P], _ST),
@@ -240,8 +240,8 @@ def dg_bin_sort(feat, radius, P, cams, n_views, tile, ws, ws_bytes, M_cap, gid, 
                             _a(ranges), _a(status), _s(stream)))
 
 
-def dg_render_workspace_size(cams, n_views, opts) -> int:
-    return _lib.dg_render_workspace_size(_c(cams), n_views, ctypes.byref(opts))
+def dg_render_workspace_size(cams, n_views, opts, M_cap=0) -> int:
+    return _lib.dg_render_workspace_size(_c(cams), n_views, ctypes.byref(opts), M_cap)
 
 
 PACKED_RECORD_BYTES = 24

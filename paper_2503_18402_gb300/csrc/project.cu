@@ -281,9 +281,9 @@ k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs
 }
 
 // Adjoint of the projection, summed over the views.  Each parameter-row
-// gradient goes to `grads` (when given) and, with ADAM, straight into the Adam
-// update of that row (params, m, v), so the fused form never stores or reloads
-// the gradient and reads the parameters once.  Each thread owns one Gaussian
+// gradient goes to `grads` (when given) and, with ADAM, to shared memory; the
+// CTA then runs the Adam update of its 128 Gaussians row by row, so the fused
+// form never stores or reloads the gradient.  Each thread owns one Gaussian
 // (one column of every row), so the in-place update races with nothing.
 // At most 128 registers (four 128-thread CTAs per SM): the adjoint streams
 // 0.5-1.5 kB per Gaussian, and the extra resident warps hide more memory
@@ -296,176 +296,189 @@ k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host,
               float* __restrict__ av, AdamHp hp)
 {
     __shared__ ViewSet s_vs;
+    __shared__ float s_g[ADAM ? DG_NPARAM : 1][128];  // ADAM: this CTA's gradients, for the row sweep
     const ViewSet& vs = block_views(vs_host, cdev, &s_vs);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P) return;
     auto put = [&](int row, float gval) {
-        const long long o = (long long)row * stride + i;
-        if (grads) grads[o] = gval;
-        if (ADAM) {
-            float p = prm[o], mm = am[o], vv = av[o];
-            adam_update(p, mm, vv, gval, adam_row(hp.lr[row], hp), hp);
-            prm[o] = p;
-            am[o] = mm;
-            av[o] = vv;
-        }
+        if (grads) grads[(long long)row * stride + i] = gval;
+        if (ADAM) s_g[row][threadIdx.x] = gval;
     };
-    G3 g;
-    gauss3d(prm, stride, i, g);
-    const float osig = 1.f / (1.f + expf(-prm[10 * stride + i]));
-    float dp[3] = {0.f, 0.f, 0.f};
-    float dsg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma (xx xy xz yy yz zz), off-diagonals counted once
-    float dop = 0.f;
-    // SH-coefficient gradients: summed over the views in registers, or, with a
-    // single view (SINGLE), emitted row by row as they are formed (no 48-float
-    // accumulator held across the kernel)
-    float dsh[SINGLE ? 1 : NB][3];
-#pragma unroll
-    for (int k = 0; k < (SINGLE ? 1 : NB); ++k) dsh[k][0] = dsh[k][1] = dsh[k][2] = 0.f;
-    bool any = false;
-    for (int v = 0; v < vs.n; ++v) {
-        const size_t r = (size_t)v * P + i;
-        if (radius[r] == 0) continue;
-        const Cam& cam = vs.cam[v];
-        Splat S;
-        if (!splat(g, cam, near_plane, eps2d, mip2d, S)) continue;
-        any = true;
-        const float4 g0 = grad2d[3 * r], g1 = grad2d[3 * r + 1], g2 = grad2d[3 * r + 2];
-        const float dLu = g0.x, dLv = g0.y, dLA = g0.z, dLB = g0.w, dLC = g1.x;
-        dop += g1.y * S.comp;  // record opacity = sigmoid * comp
-        const uint8_t cm = clampm[r];
-        const float dcol[3] = {(cm & 1u) ? 0.f : g1.z, (cm & 2u) ? 0.f : g1.w, (cm & 4u) ? 0.f : g2.x};
-        // colour: SH coefficients and the view direction
-        {
-            float d0 = g.p[0] - vs.campos[v][0], d1 = g.p[1] - vs.campos[v][1], d2 = g.p[2] - vs.campos[v][2];
-            const float len = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-            const float linv = 1.f / len;
-            d0 *= linv; d1 *= linv; d2 *= linv;
-            float Y[16], D[16][3];
-            sh_values(d0, d1, d2, Y);
-            sh_partials(d0, d1, d2, D);
-            float gd[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-            for (int k = 0; k < NB; ++k)
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    const float cw = dcol[ch] * prm[(11 + 3 * k + ch) * stride + i];
-                    gd[0] += cw * D[k][0];
-                    gd[1] += cw * D[k][1];
-                    gd[2] += cw * D[k][2];
-                    if (SINGLE) put(11 + 3 * k + ch, Y[k] * dcol[ch]);  // after the coefficient was read
-                    else dsh[SINGLE ? 0 : k][ch] += Y[k] * dcol[ch];
-                }
-            const float dd = d0 * gd[0] + d1 * gd[1] + d2 * gd[2];
-            dp[0] += (gd[0] - d0 * dd) * linv;
-            dp[1] += (gd[1] - d1 * dd) * linv;
-            dp[2] += (gd[2] - d2 * dd) * linv;
+    auto adjoint = [&]() {
+        G3 g;
+        gauss3d(prm, stride, i, g);
+        const float osig = 1.f / (1.f + expf(-prm[10 * stride + i]));
+        float dp[3] = {0.f, 0.f, 0.f};
+        float dsg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma (xx xy xz yy yz zz), off-diagonals counted once
+        float dop = 0.f;
+        // SH-coefficient gradients: summed over the views in registers, or, with a
+        // single view (SINGLE), emitted row by row as they are formed (no 48-float
+        // accumulator held across the kernel)
+        float dsh[SINGLE ? 1 : NB][3];
+    #pragma unroll
+        for (int k = 0; k < (SINGLE ? 1 : NB); ++k) dsh[k][0] = dsh[k][1] = dsh[k][2] = 0.f;
+        bool any = false;
+        for (int v = 0; v < vs.n; ++v) {
+            const size_t r = (size_t)v * P + i;
+            if (radius[r] == 0) continue;
+            const Cam& cam = vs.cam[v];
+            Splat S;
+            if (!splat(g, cam, near_plane, eps2d, mip2d, S)) continue;
+            any = true;
+            const float4 g0 = grad2d[3 * r], g1 = grad2d[3 * r + 1], g2 = grad2d[3 * r + 2];
+            const float dLu = g0.x, dLv = g0.y, dLA = g0.z, dLB = g0.w, dLC = g1.x;
+            dop += g1.y * S.comp;  // record opacity = sigmoid * comp
+            const uint8_t cm = clampm[r];
+            const float dcol[3] = {(cm & 1u) ? 0.f : g1.z, (cm & 2u) ? 0.f : g1.w, (cm & 4u) ? 0.f : g2.x};
+            // colour: SH coefficients and the view direction
+            {
+                float d0 = g.p[0] - vs.campos[v][0], d1 = g.p[1] - vs.campos[v][1], d2 = g.p[2] - vs.campos[v][2];
+                const float len = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+                const float linv = 1.f / len;
+                d0 *= linv; d1 *= linv; d2 *= linv;
+                float Y[16], D[16][3];
+                sh_values(d0, d1, d2, Y);
+                sh_partials(d0, d1, d2, D);
+                float gd[3] = {0.f, 0.f, 0.f};
+    #pragma unroll
+                for (int k = 0; k < NB; ++k)
+    #pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) {
+                        const float cw = dcol[ch] * prm[(11 + 3 * k + ch) * stride + i];
+                        gd[0] += cw * D[k][0];
+                        gd[1] += cw * D[k][1];
+                        gd[2] += cw * D[k][2];
+                        if (SINGLE) put(11 + 3 * k + ch, Y[k] * dcol[ch]);  // after the coefficient was read
+                        else dsh[SINGLE ? 0 : k][ch] += Y[k] * dcol[ch];
+                    }
+                const float dd = d0 * gd[0] + d1 * gd[1] + d2 * gd[2];
+                dp[0] += (gd[0] - d0 * dd) * linv;
+                dp[1] += (gd[1] - d1 * dd) * linv;
+                dp[2] += (gd[2] - d2 * dd) * linv;
+            }
+            const float tx = S.t[0], ty = S.t[1], tz = S.t[2];
+            const float iz = 1.f / tz, iz2 = iz * iz;
+            float dt[3];
+            dt[0] = dLu * cam.fx * iz;
+            dt[1] = dLv * cam.fy * iz;
+            dt[2] = -(dLu * cam.fx * tx + dLv * cam.fy * ty) * iz2;
+            // conic -> 2D covariance: Gm = -K Gk K, Gk = [[dA, dB/2], [dB/2, dC]]
+            const float A = S.A, B = S.B, C = S.C;
+            const float k00 = A * dLA + 0.5f * B * dLB, k01 = 0.5f * A * dLB + B * dLC;
+            const float k10 = B * dLA + 0.5f * C * dLB, k11 = 0.5f * B * dLB + C * dLC;
+            float gm00 = -(k00 * A + k01 * B);
+            float gm01 = -(k00 * B + k01 * C);
+            float gm11 = -(k10 * B + k11 * C);
+            if (mip2d > 0.f && S.det0 > 0.f) {
+                // 2D filter: d sqrt(det0 / det) per covariance entry (det0 of the
+                // undilated, det of the filtered matrix; the off-diagonal entry
+                // carries half of the derivative in b)
+                const float h = 0.5f * S.comp * g1.y * osig;
+                const float a0 = S.a - mip2d, c0 = S.c - mip2d;
+                const float i0 = 1.f / S.det0, i1 = 1.f / S.det;
+                gm00 += h * (c0 * i0 - S.c * i1);
+                gm11 += h * (a0 * i0 - S.a * i1);
+                gm01 += h * (S.b * i1 - S.b * i0);
+            }
+            // Sigma2 = T2 Sigma T2^T:  dSigma = T2^T Gm T2,  dT2 = 2 Gm T2 Sigma
+            const float* t2 = S.t2;
+            float gt[6];  // Gm T2
+    #pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                gt[c] = gm00 * t2[c] + gm01 * t2[3 + c];
+                gt[3 + c] = gm01 * t2[c] + gm11 * t2[3 + c];
+            }
+            // symmetric dSigma accumulated as 6 unique entries of the full-matrix gradient
+            dsg[0] += t2[0] * gt[0] + t2[3] * gt[3];
+            dsg[1] += t2[0] * gt[1] + t2[3] * gt[4];
+            dsg[2] += t2[0] * gt[2] + t2[3] * gt[5];
+            dsg[3] += t2[1] * gt[1] + t2[4] * gt[4];
+            dsg[4] += t2[1] * gt[2] + t2[4] * gt[5];
+            dsg[5] += t2[2] * gt[2] + t2[5] * gt[5];
+            const float* sg = g.sig;
+            const float sgm[9] = {sg[0], sg[1], sg[2], sg[1], sg[3], sg[4], sg[2], sg[4], sg[5]};
+            float dt2[6];
+    #pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+    #pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    dt2[3 * rr + c] = 2.f * (gt[3 * rr] * sgm[c] + gt[3 * rr + 1] * sgm[3 + c] + gt[3 * rr + 2] * sgm[6 + c]);
+            // T2 = J Rc
+            const float* rc = cam.r;
+            const float dj00 = dt2[0] * rc[0] + dt2[1] * rc[1] + dt2[2] * rc[2];
+            const float dj02 = dt2[0] * rc[6] + dt2[1] * rc[7] + dt2[2] * rc[8];
+            const float dj11 = dt2[3] * rc[3] + dt2[4] * rc[4] + dt2[5] * rc[5];
+            const float dj12 = dt2[3] * rc[6] + dt2[4] * rc[7] + dt2[5] * rc[8];
+            dt[2] -= (dj00 * cam.fx + dj11 * cam.fy) * iz2;
+            if (!S.gx) {
+                dt[0] -= dj02 * cam.fx * iz2;
+                dt[2] += dj02 * 2.f * cam.fx * tx * iz2 * iz;
+            } else {
+                dt[2] += dj02 * cam.fx * S.lx * iz2;
+            }
+            if (!S.gy) {
+                dt[1] -= dj12 * cam.fy * iz2;
+                dt[2] += dj12 * 2.f * cam.fy * ty * iz2 * iz;
+            } else {
+                dt[2] += dj12 * cam.fy * S.ly * iz2;
+            }
+            // t = Rc p + t_c
+    #pragma unroll
+            for (int c = 0; c < 3; ++c) dp[c] += rc[c] * dt[0] + rc[3 + c] * dt[1] + rc[6 + c] * dt[2];
         }
-        const float tx = S.t[0], ty = S.t[1], tz = S.t[2];
-        const float iz = 1.f / tz, iz2 = iz * iz;
-        float dt[3];
-        dt[0] = dLu * cam.fx * iz;
-        dt[1] = dLv * cam.fy * iz;
-        dt[2] = -(dLu * cam.fx * tx + dLv * cam.fy * ty) * iz2;
-        // conic -> 2D covariance: Gm = -K Gk K, Gk = [[dA, dB/2], [dB/2, dC]]
-        const float A = S.A, B = S.B, C = S.C;
-        const float k00 = A * dLA + 0.5f * B * dLB, k01 = 0.5f * A * dLB + B * dLC;
-        const float k10 = B * dLA + 0.5f * C * dLB, k11 = 0.5f * B * dLB + C * dLC;
-        float gm00 = -(k00 * A + k01 * B);
-        float gm01 = -(k00 * B + k01 * C);
-        float gm11 = -(k10 * B + k11 * C);
-        if (mip2d > 0.f && S.det0 > 0.f) {
-            // 2D filter: d sqrt(det0 / det) per covariance entry (det0 of the
-            // undilated, det of the filtered matrix; the off-diagonal entry
-            // carries half of the derivative in b)
-            const float h = 0.5f * S.comp * g1.y * osig;
-            const float a0 = S.a - mip2d, c0 = S.c - mip2d;
-            const float i0 = 1.f / S.det0, i1 = 1.f / S.det;
-            gm00 += h * (c0 * i0 - S.c * i1);
-            gm11 += h * (a0 * i0 - S.a * i1);
-            gm01 += h * (S.b * i1 - S.b * i0);
+        if (!any) {
+            for (int rr = 0; rr < DG_NPARAM; ++rr) put(rr, 0.f);
+            return;
         }
-        // Sigma2 = T2 Sigma T2^T:  dSigma = T2^T Gm T2,  dT2 = 2 Gm T2 Sigma
-        const float* t2 = S.t2;
-        float gt[6];  // Gm T2
-#pragma unroll
+        put(0, dp[0]);
+        put(1, dp[1]);
+        put(2, dp[2]);
+        put(10, dop * osig * (1.f - osig));
+    #pragma unroll
+        for (int k = SINGLE ? NB : 0; k < 16; ++k)
+    #pragma unroll
+            for (int ch = 0; ch < 3; ++ch) put(11 + 3 * k + ch, k < NB ? dsh[SINGLE ? 0 : k][ch] : 0.f);
+        // Sigma = M M^T:  dM = 2 dSigma M;  M = Rq diag(s)
+        const float ds[9] = {dsg[0], dsg[1], dsg[2], dsg[1], dsg[3], dsg[4], dsg[2], dsg[4], dsg[5]};
+        float dR[9];
+    #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            gt[c] = gm00 * t2[c] + gm01 * t2[3 + c];
-            gt[3 + c] = gm01 * t2[c] + gm11 * t2[3 + c];
+            float dsc = 0.f;
+    #pragma unroll
+            for (int rr = 0; rr < 3; ++rr) {
+                const float dm = 2.f * (ds[3 * rr] * g.m[c] + ds[3 * rr + 1] * g.m[3 + c] + ds[3 * rr + 2] * g.m[6 + c]);
+                dsc += dm * g.rq[3 * rr + c];
+                dR[3 * rr + c] = dm * g.s[c];
+            }
+            put(3 + c, dsc * g.s[c]);
         }
-        // symmetric dSigma accumulated as 6 unique entries of the full-matrix gradient
-        dsg[0] += t2[0] * gt[0] + t2[3] * gt[3];
-        dsg[1] += t2[0] * gt[1] + t2[3] * gt[4];
-        dsg[2] += t2[0] * gt[2] + t2[3] * gt[5];
-        dsg[3] += t2[1] * gt[1] + t2[4] * gt[4];
-        dsg[4] += t2[1] * gt[2] + t2[4] * gt[5];
-        dsg[5] += t2[2] * gt[2] + t2[5] * gt[5];
-        const float* sg = g.sig;
-        const float sgm[9] = {sg[0], sg[1], sg[2], sg[1], sg[3], sg[4], sg[2], sg[4], sg[5]};
-        float dt2[6];
-#pragma unroll
-        for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                dt2[3 * rr + c] = 2.f * (gt[3 * rr] * sgm[c] + gt[3 * rr + 1] * sgm[3 + c] + gt[3 * rr + 2] * sgm[6 + c]);
-        // T2 = J Rc
-        const float* rc = cam.r;
-        const float dj00 = dt2[0] * rc[0] + dt2[1] * rc[1] + dt2[2] * rc[2];
-        const float dj02 = dt2[0] * rc[6] + dt2[1] * rc[7] + dt2[2] * rc[8];
-        const float dj11 = dt2[3] * rc[3] + dt2[4] * rc[4] + dt2[5] * rc[5];
-        const float dj12 = dt2[3] * rc[6] + dt2[4] * rc[7] + dt2[5] * rc[8];
-        dt[2] -= (dj00 * cam.fx + dj11 * cam.fy) * iz2;
-        if (!S.gx) {
-            dt[0] -= dj02 * cam.fx * iz2;
-            dt[2] += dj02 * 2.f * cam.fx * tx * iz2 * iz;
-        } else {
-            dt[2] += dj02 * cam.fx * S.lx * iz2;
+        const float w = g.qn[0], x = g.qn[1], y = g.qn[2], z = g.qn[3];
+        float dq[4];
+        dq[0] = 2.f * (z * (dR[3] - dR[1]) + y * (dR[2] - dR[6]) + x * (dR[7] - dR[5]));
+        dq[1] = 2.f * (y * (dR[1] + dR[3]) + z * (dR[2] + dR[6]) + w * (dR[7] - dR[5]) - 2.f * x * (dR[4] + dR[8]));
+        dq[2] = 2.f * (x * (dR[1] + dR[3]) + w * (dR[2] - dR[6]) + z * (dR[5] + dR[7]) - 2.f * y * (dR[0] + dR[8]));
+        dq[3] = 2.f * (w * (dR[3] - dR[1]) + x * (dR[2] + dR[6]) + y * (dR[5] + dR[7]) - 2.f * z * (dR[0] + dR[4]));
+        const float qd = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
+    #pragma unroll
+        for (int c = 0; c < 4; ++c) put(6 + c, (dq[c] - g.qn[c] * qd) * g.qinv);
+
+    };
+    if (i < P) adjoint();
+    if (ADAM) {
+        // Adam over the CTA's [59][128] tile: one coalesced row at a time, every
+        // row's loads independent of the previous row's update
+        __syncthreads();
+        if (i < P) {
+#pragma unroll 4
+            for (int r = 0; r < DG_NPARAM; ++r) {
+                const long long o = (long long)r * stride + i;
+                float p = prm[o], mm = am[o], vv = av[o];
+                adam_update(p, mm, vv, s_g[r][threadIdx.x], adam_row(hp.lr[r], hp), hp);
+                prm[o] = p;
+                am[o] = mm;
+                av[o] = vv;
+            }
         }
-        if (!S.gy) {
-            dt[1] -= dj12 * cam.fy * iz2;
-            dt[2] += dj12 * 2.f * cam.fy * ty * iz2 * iz;
-        } else {
-            dt[2] += dj12 * cam.fy * S.ly * iz2;
-        }
-        // t = Rc p + t_c
-#pragma unroll
-        for (int c = 0; c < 3; ++c) dp[c] += rc[c] * dt[0] + rc[3 + c] * dt[1] + rc[6 + c] * dt[2];
     }
-    if (!any) {
-        for (int rr = 0; rr < DG_NPARAM; ++rr) put(rr, 0.f);
-        return;
-    }
-    put(0, dp[0]);
-    put(1, dp[1]);
-    put(2, dp[2]);
-    put(10, dop * osig * (1.f - osig));
-#pragma unroll
-    for (int k = SINGLE ? NB : 0; k < 16; ++k)
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) put(11 + 3 * k + ch, k < NB ? dsh[SINGLE ? 0 : k][ch] : 0.f);
-    // Sigma = M M^T:  dM = 2 dSigma M;  M = Rq diag(s)
-    const float ds[9] = {dsg[0], dsg[1], dsg[2], dsg[1], dsg[3], dsg[4], dsg[2], dsg[4], dsg[5]};
-    float dR[9];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        float dsc = 0.f;
-#pragma unroll
-        for (int rr = 0; rr < 3; ++rr) {
-            const float dm = 2.f * (ds[3 * rr] * g.m[c] + ds[3 * rr + 1] * g.m[3 + c] + ds[3 * rr + 2] * g.m[6 + c]);
-            dsc += dm * g.rq[3 * rr + c];
-            dR[3 * rr + c] = dm * g.s[c];
-        }
-        put(3 + c, dsc * g.s[c]);
-    }
-    const float w = g.qn[0], x = g.qn[1], y = g.qn[2], z = g.qn[3];
-    float dq[4];
-    dq[0] = 2.f * (z * (dR[3] - dR[1]) + y * (dR[2] - dR[6]) + x * (dR[7] - dR[5]));
-    dq[1] = 2.f * (y * (dR[1] + dR[3]) + z * (dR[2] + dR[6]) + w * (dR[7] - dR[5]) - 2.f * x * (dR[4] + dR[8]));
-    dq[2] = 2.f * (x * (dR[1] + dR[3]) + w * (dR[2] - dR[6]) + z * (dR[5] + dR[7]) - 2.f * y * (dR[0] + dR[8]));
-    dq[3] = 2.f * (w * (dR[3] - dR[1]) + x * (dR[2] + dR[6]) + y * (dR[5] + dR[7]) - 2.f * z * (dR[0] + dR[4]));
-    const float qd = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) put(6 + c, (dq[c] - g.qn[c] * qd) * g.qinv);
 }
 
 }  // namespace dg

@@ -329,7 +329,7 @@ template <int B, int PPT, bool PROD, int REC>
 __global__ void __launch_bounds__(B * B / PPT)
 k_render_fwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
              const uint2* __restrict__ ranges, RViews rv, RHdr* hdr, const int4* __restrict__ items,
-             const int4* __restrict__ sitems, Slots sl,
+             const int4* __restrict__ sitems, Slots sl, uint8_t* __restrict__ flags, long long flags_cap,
              float* __restrict__ img, float* __restrict__ Tout, int* __restrict__ lastout,
              int* __restrict__ exout, int* __restrict__ blout)
 {
@@ -338,6 +338,7 @@ k_render_fwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
     __shared__ float4 s_a[NT];    // u, v, a', b'  (prescaled conic, see below)
     __shared__ float2 s_q[NT];    // c', log2 o
     __shared__ float4 s_col[NT];  // r, g, b, list position (int bits)
+    __shared__ uint8_t s_bl[NT];  // staged entry blended by some pixel of the item
     __shared__ int s_w[NT / 32];
     __shared__ int4 s_item;
     const bool planned = hdr->planned != 0 && items != nullptr;
@@ -400,6 +401,7 @@ k_render_fwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
             s_a[slot] = make_float4(ga.x, ga.y, -0.5f * kLog2e * ga.z, -kLog2e * ga.w);
             s_q[slot] = make_float2(-0.5f * kLog2e * gb.x, __log2f(gb.y));
             s_col[slot] = make_float4(gb.z, gb.w, gc, __int_as_float(j));
+            s_bl[slot] = 0;
         }
         __syncthreads();
         // Eq. 1 for entry kk at the thread's pixel k, given the entry's power p
@@ -422,6 +424,7 @@ k_render_fwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                     c2[k] += w * col.z;
                     last[k] = pos + 1;
                     ++nbl[k];
+                    s_bl[kk] = 1;
                 }
                 T[k] = Tn;
             }
@@ -450,6 +453,13 @@ k_render_fwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
             alldone = true;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) alldone = alldone && done[k];
+        }
+        if (!PROD && flags) {
+            // per list entry: blended by some pixel of this item (the backward
+            // stages only those); every entry of the batch gets its byte
+            __syncthreads();
+            const long long gj = (long long)rg.x + j;
+            if (j < hi && gj < flags_cap) flags[gj] = keep ? s_bl[slot] : 0;
         }
     }
     if (split) {
@@ -594,6 +604,7 @@ template <int B, int PPT, int REC>
 __global__ void __launch_bounds__(B * B / PPT)
 k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
              const uint2* __restrict__ ranges, RViews rv, RHdr* hdr, const int4* __restrict__ items, Slots sl,
+             const uint8_t* __restrict__ flags, long long flags_cap,
              const float* __restrict__ Tfin, const int* __restrict__ lastin,
              const float* __restrict__ dLdimg, float4* __restrict__ grad2d)
 {
@@ -672,9 +683,20 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
         float gc = 0.f;
         uint32_t g = 0;
         if (j < top) {
-            g = gid[rg.x + j];
-            load_record<REC>(feat, g, ga, gb, gc);
-            keep = !tile_skip(ga, gb, tpx0, tpx1, tpy0, tpy1);
+            const long long gj = (long long)rg.x + j;
+            if (flags && gj < flags_cap) {
+                // the forward's record of this entry: blended by some pixel of the
+                // tile or not (an entry no pixel blended has no gradient)
+                keep = flags[gj] != 0;
+                if (keep) {
+                    g = gid[gj];
+                    load_record<REC>(feat, g, ga, gb, gc);
+                }
+            } else {
+                g = gid[gj];
+                load_record<REC>(feat, g, ga, gb, gc);
+                keep = !tile_skip(ga, gb, tpx0, tpx1, tpy0, tpy1);
+            }
         }
         int cnt;
         const int slot = compact_index<NT>(keep, s_w, &cnt);
@@ -794,6 +816,8 @@ static int resident_ctas(Kern kern, int threads)
 // Layout of the render workspace for n_tiles tiles of edge B.
 struct RenderWs {
     dg::RHdr* hdr;
+    uint8_t* flags;       // per pair: blended by some pixel of its tile (written by the forward)
+    long long flags_cap;  // pairs the flag array holds
     int4* items;
     int4* sitems;
     uint64_t* toff;
@@ -808,7 +832,19 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Chunk slots: 2^20 pixels' worth (32 MiB of per-pixel chunk state).
 static int slot_cap(int B) { return (1 << 20) / (B * B); }
 
-static RenderWs render_ws(void* base, long long n_tiles, int B, bool split)
+// Layout of the render workspace; the per-pair flag array takes whatever
+// follows the fixed part (ws_bytes - fixed bytes).
+static RenderWs render_ws_fixed(void* base, long long n_tiles, int B, bool split);
+static RenderWs render_ws(void* base, long long n_tiles, int B, bool split, size_t ws_bytes = 0)
+{
+    RenderWs w = render_ws_fixed(base, n_tiles, B, split);
+    w.flags = (uint8_t*)base + w.bytes;
+    w.flags_cap = ws_bytes > w.bytes ? (long long)(ws_bytes - w.bytes) : 0;
+    if (!base) w.flags = nullptr;
+    return w;
+}
+
+static RenderWs render_ws_fixed(void* base, long long n_tiles, int B, bool split)
 {
     RenderWs w{};
     char* p = (char*)base;
@@ -856,12 +892,12 @@ static dg_status launch_fwd(const float* feat, const uint32_t* gid, const uint32
         dg::k_plan_items<<<pg < 1024 ? pg : 1024, 256, 0, s>>>(rg, (int)n, w.hdr, cfg, w.toff, w.items, w.sitems);
         auto kprod = dg::k_render_fwd<B, PPT, true, REC>;
         kprod<<<resident_ctas(kprod, B * B / PPT), B * B / PPT, 0, s>>>(
-            (const void*)feat, gid, rg, rv, w.hdr, w.items, w.sitems, w.sl, img, T, last, ex, bl);
+            (const void*)feat, gid, rg, rv, w.hdr, w.items, w.sitems, w.sl, nullptr, 0, img, T, last, ex, bl);
         dg_note_launch(2);
     }
     const int grid = split ? R : (R < rv.total ? R : (rv.total > 0 ? rv.total : 1));
-    kern<<<grid, B * B / PPT, 0, s>>>((const void*)feat, gid, rg, rv, w.hdr, w.items, w.sitems, w.sl, img, T,
-                                      last, ex, bl);
+    kern<<<grid, B * B / PPT, 0, s>>>((const void*)feat, gid, rg, rv, w.hdr, w.items, w.sitems, w.sl, w.flags,
+                                      w.flags_cap, img, T, last, ex, bl);
     dg_note_launch();
     if (split) {
         int dev = 0, sms = 0;
@@ -881,8 +917,8 @@ static void launch_bwd(const float* feat, const uint32_t* gid, const uint32_t* r
     auto kern = dg::k_render_bwd<B, PPT, REC>;
     const int grid = resident_ctas(kern, B * B / PPT);
     cudaMemsetAsync(&w.hdr->cnt_bwd, 0, sizeof(int), s);
-    kern<<<grid, B * B / PPT, 0, s>>>((const void*)feat, gid, (const uint2*)ranges, rv, w.hdr, w.items, w.sl, T,
-                                      last, dL, (float4*)g2);
+    kern<<<grid, B * B / PPT, 0, s>>>((const void*)feat, gid, (const uint2*)ranges, rv, w.hdr, w.items, w.sl,
+                                      w.flags, w.flags_cap, T, last, dL, (float4*)g2);
     dg_note_launch();
 }
 
@@ -939,18 +975,22 @@ static bool render_args(const dg_camera* cams, int n_views, const dg_raster_opts
     if (p != 0 && p != 1 && p != 2 && p != 4) { dg_set_error("pixels_per_thread must be 0, 1, 2 or 4, got %d", p); return false; }
     if (total_tiles(cams, n_views, opts->tile) >= (1LL << 30)) { dg_set_error("too many tiles"); return false; }
     if (opts->record != 0 && opts->record != 1) { dg_set_error("record must be 0 (float32) or 1 (mixed), got %d", opts->record); return false; }
-    const size_t need = dg_render_workspace_size(cams, n_views, opts);
+    const size_t need = dg_render_workspace_size(cams, n_views, opts, 0);  // the fixed part; flags use the rest
     if (!ws || ws_bytes < need) { dg_set_error("render workspace missing or too small (%zu < %zu bytes)", ws_bytes, need); return false; }
     if (((uintptr_t)ws) & 255u) { dg_set_error("render workspace must be 256-byte aligned"); return false; }
     return true;
 }
 
-extern "C" size_t dg_render_workspace_size(const dg_camera* cams, int32_t n_views, const dg_raster_opts* opts)
+extern "C" size_t dg_render_workspace_size(const dg_camera* cams, int32_t n_views, const dg_raster_opts* opts,
+                                           int64_t M_cap)
 {
     if (!cams || !opts || n_views < 1 || n_views > DG_MAX_VIEWS || (opts->tile != 8 && opts->tile != 16)) return 0;
+    if (M_cap < 0) return 0;
     for (int v = 0; v < n_views; ++v)
         if (cams[v].width <= 0 || cams[v].height <= 0) return 0;
-    return render_ws(nullptr, total_tiles(cams, n_views, opts->tile), opts->tile, opts->split_len >= 0).bytes;
+    const size_t fixed = render_ws_fixed(nullptr, total_tiles(cams, n_views, opts->tile), opts->tile,
+                                         opts->split_len >= 0).bytes;
+    return fixed + (((size_t)M_cap + 255) & ~(size_t)255);
 }
 
 extern "C" dg_status dg_render_fwd(const float* feat, const uint32_t* gid, const uint32_t* ranges,
@@ -964,7 +1004,7 @@ extern "C" dg_status dg_render_fwd(const float* feat, const uint32_t* gid, const
     cudaStream_t s = (cudaStream_t)stream;
     const int B = opts->tile;
     const dg::RViews rv = make_rviews(cams, n_views, B, opts);
-    const RenderWs w = render_ws(ws, rv.total, B, opts->split_len >= 0);
+    const RenderWs w = render_ws(ws, rv.total, B, opts->split_len >= 0, ws_bytes);
     const int sp = opts->split_len;
     const int ppt = resolve_ppt(opts, false);
     if (opts->record == 1) fwd_dispatch<1>(B, ppt, feat, gid, ranges, rv, w, sp, img, T_final, last, examined, blended, s);
@@ -985,7 +1025,7 @@ extern "C" dg_status dg_render_bwd(const float* feat, const uint32_t* gid, const
     if (n_records > 0) cudaMemsetAsync(grad2d, 0, sizeof(float) * DG_FEAT_FLOATS * (size_t)n_records, s);
     const int B = opts->tile;
     const dg::RViews rv = make_rviews(cams, n_views, B, opts);
-    const RenderWs w = render_ws(ws, rv.total, B, opts->split_len >= 0);
+    const RenderWs w = render_ws(ws, rv.total, B, opts->split_len >= 0, ws_bytes);
     const int ppt = resolve_ppt(opts, true);
     if (opts->record == 1) bwd_dispatch<1>(B, ppt, feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);
     else bwd_dispatch<0>(B, ppt, feat, gid, ranges, rv, w, T_final, last, dL_dimg, grad2d, s);

@@ -115,7 +115,7 @@ class Rasterizer:
             self.n_tiles = n_tiles
 
     def _ensure_rws(self, carr, V):
-        need = capi.dg_render_workspace_size(carr, V, self.opts_fwd)
+        need = capi.dg_render_workspace_size(carr, V, self.opts_fwd, self.M_cap)
         if self.rws is None or self.rws.numel() < need:
             self.rws = torch.empty(need, dtype=torch.uint8, device=self.device)
 

@@ -51,7 +51,7 @@ def test_binding_covers_every_export():
 
 def test_host_only_calls_without_gpu():
     from paper_2503_18402_gb300 import capi
-    assert capi.dg_abi_version() == 3
+    assert capi.dg_abi_version() == 4
     assert capi.dg_bin_workspace_size(1000, 1, 5000) > 5000 * 16
     assert capi.dg_bin_workspace_size(1000, 4, 5000) > capi.dg_bin_workspace_size(1000, 1, 5000)
     assert capi.dg_bin_workspace_size(-1, 1, 0) == 0
@@ -60,6 +60,8 @@ def test_host_only_calls_without_gpu():
     nosplit = capi.dg_render_workspace_size(cam1, 1, capi.raster_opts(split_len=-1))
     split = capi.dg_render_workspace_size(cam1, 1, capi.raster_opts())
     assert nosplit >= 16 and split > nosplit
+    # one flag byte per pair on top of the fixed part
+    assert capi.dg_render_workspace_size(cam1, 1, capi.raster_opts(), 1 << 20) == split + (1 << 20)
     big = capi.camera([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 4], 50, 50, 32, 32, 1600, 1063)
     assert capi.dg_render_workspace_size([big] * 16, 16, capi.raster_opts(tile=8)) > \
         capi.dg_render_workspace_size(big, 1, capi.raster_opts(tile=8))

@@ -682,3 +682,32 @@ def test_mip_2d_filter_matches_oracle():
     og = oracle.project_bwd(g64, ocam, k, g2.astype(np.float64))
     ok, worst, nbad = G.grad_close(G.np_(grads).T, og)
     assert ok, (worst, nbad)
+
+
+def test_backward_with_and_without_blend_flags():
+    """The backward stages only entries the forward flagged as blended by some
+    pixel of their tile; without room for the flags it falls back to the tile
+    test.  Both give the same gradients (only float addition order differs)."""
+    g = synth.random_gaussians(5000, 123)
+    g[:, 3:6] += 0.2
+    cam = G.gpu_camera(synth.camera_cfg0(130, 99, 4.0))
+    P = g.shape[0]
+    params = G.gpu_params(g)
+    out = []
+    for with_flags in (True, False):
+        rz = Rasterizer("cuda", capi.raster_opts(tile=8))
+        fr = rz.forward(params, P, cam)
+        if not with_flags:  # re-render into a workspace without the flag bytes
+            carr = capi.cameras([cam])
+            rz.rws = torch.empty(capi.dg_render_workspace_size(carr, 1, rz.opts_fwd, 0), dtype=torch.uint8,
+                                 device="cuda")
+            capi.dg_render_fwd(rz.rfeat, rz.gid, rz.ranges, carr, 1, rz.opts_fwd, fr.flat_img, fr.flat_T,
+                               fr.flat_last, None, None, rz.rws, rz.rws.numel())
+        rng = np.random.default_rng(8)
+        dL = torch.from_numpy((rng.normal(size=(3, 99, 130)) / 1e4).astype(np.float32)).cuda()
+        rz.backward_render(fr, dL)
+        torch.cuda.synchronize()
+        out.append(G.np_(rz.grad2d[:P]).copy())
+    ok, worst, nbad = G.grad_close(out[0], out[1])
+    assert ok, (worst, nbad)
+    assert np.abs(out[0]).max() > 0
