@@ -383,8 +383,19 @@ k_render_fwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
     bool alldone = true;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) alldone = alldone && done[k];
+    // flag bytes of the previous batch, written once the next barrier has
+    // passed (every lane's blends of that batch are then in s_bl, and the next
+    // staging writes s_bl only after compact_index's barriers)
+    int pj = -1, pslot = 0;
+    bool pkeep = false;
+    auto write_flags = [&]() {
+        if (PROD || !flags || pj < 0) return;
+        const long long gj = (long long)rg.x + pj;
+        if (pj < hi && gj < flags_cap) flags[gj] = pkeep ? s_bl[pslot] : 0;
+    };
     for (int base = lo; base < hi; base += NT) {
         if (__syncthreads_count(alldone) == NT) break;
+        write_flags();
         const int j = base + (int)threadIdx.x;
         bool keep = false;
         float4 ga, gb;
@@ -454,13 +465,15 @@ k_render_fwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
 #pragma unroll
             for (int k = 0; k < PPT; ++k) alldone = alldone && done[k];
         }
-        if (!PROD && flags) {
-            // per list entry: blended by some pixel of this item (the backward
-            // stages only those); every entry of the batch gets its byte
-            __syncthreads();
-            const long long gj = (long long)rg.x + j;
-            if (j < hi && gj < flags_cap) flags[gj] = keep ? s_bl[slot] : 0;
-        }
+        // per list entry: blended by some pixel of this item (the backward
+        // stages only those); every entry of the batch gets its byte
+        pj = j;
+        pkeep = keep;
+        pslot = slot;
+    }
+    if (!PROD && flags) {
+        __syncthreads();
+        write_flags();
     }
     if (split) {
         const size_t s0 = (size_t)(it.slot0 + it.c) * NPIX;
