@@ -70,6 +70,25 @@ def config(args, n_gauss, shape=None):
             "l2": "working set 1.9 GB > L2 (no flush)", "parallelism": f"replicas{args.gpus}"}
 
 
+# --------------------------------------------------------------------------- ranks
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value of x over the ranks (replicas run in lockstep between
+    barriers, so the job takes as long as its slowest rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_ms_per_view(elapsed_ms: float, steps: int, world: int) -> float:
+    """Whole-job figure: every rank renders `steps` views (weak scaling), the
+    job takes the slowest rank's time."""
+    return elapsed_ms / (steps * world)
+
+
 # --------------------------------------------------------------------------- scene
 def make_scene(n_gauss, rank):
     from paper_2503_18402_gb300 import synth
@@ -260,10 +279,7 @@ def run_ours(args):
             continue
         stage_ms[name] = stage_ms.get(name, 0.0) + prev.elapsed_time(e)
         prev = e
-    if world > 1:
-        tt = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, world, dev)
 
     # the same step captured once as a CUDA graph and replayed per view (new
     # camera, Adam hyper-parameters and target written to device buffers)
@@ -316,13 +332,10 @@ def run_ours(args):
         float(loss[1].item())
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - e0) * 1e3
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
 
     views_total = args.steps * world
-    ms_per_view = elapsed_ms / views_total
+    ms_per_view = job_ms_per_view(elapsed_ms, args.steps, world)
     out = {
         "metric": "fwd+bwd rasterize ms/view (full-res training step incl. L1 + Adam)",
         "value": round(ms_per_view, 4), "unit": "ms/view", "n_gpus": world, "steps": args.steps,
