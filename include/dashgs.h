@@ -177,7 +177,10 @@ DG_API dg_status dg_bin_count(const float* depth, const int32_t* tiles, int64_t 
  * Out: gid    [M_cap] uint32, record index v * P + i of each sorted pair;
  *      ranges [2 * total tiles] uint32, [start, end) of each tile's list;
  *      status (device int32): 0, or DG_ERR_CAPACITY when M > M_cap, in which
- *              case gid is untouched and every range is empty.
+ *              case gid is untouched and every range is empty, or
+ *              DG_ERR_TIMEOUT when a bounded wait between thread blocks of
+ *              phase 1 gave up (lists not valid; does not happen when the
+ *              device runs the launch to completion).
  * feat/radius are dg_project's outputs for the same P and cameras. */
 DG_API dg_status dg_bin_sort(const float* feat, const int32_t* radius, int64_t P, const dg_camera* cams,
                       int32_t n_views, int32_t tile, void* ws, size_t ws_bytes, int64_t M_cap, uint32_t* gid,
