@@ -654,7 +654,10 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
     const int lo = split ? it.c * L : 0;
     const int hi = split ? (int)min((long long)nlist, (long long)lo + L) : nlist;
     const size_t HW = (size_t)W * H;
-    float pyc[PPT], T[PPT], g0[PPT], g1[PPT], g2[PPT], S0[PPT], S1[PPT], S2[PPT];
+    // per pixel: transmittance, dL/dC, and gS = dL/dC . S where S is the
+    // colour composited behind the current entry (the only way S enters the
+    // gradient: dL/dalpha_j = T_j (g . c_j) - (g . S_j) / (1 - alpha_j))
+    float pyc[PPT], T[PPT], g0[PPT], g1[PPT], g2[PPT], gS[PPT];
     int lastp[PPT];
     int mylast = 0;
 #pragma unroll
@@ -662,7 +665,7 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
         const int y = y0 + k;
         pyc[k] = (float)y + 0.5f;
         T[k] = 1.f; g0[k] = g1[k] = g2[k] = 0.f; lastp[k] = 0;
-        S0[k] = S1[k] = S2[k] = 0.f;
+        gS[k] = 0.f;
         if (x < W && y < H) {
             const size_t pix = (size_t)y * W + x;
             const float* dl = dLdimg + 3 * it.poff;
@@ -674,10 +677,10 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                 // the chunk's end transmittance and the colour behind the chunk
                 const size_t s = (size_t)(it.slot0 + it.c) * NPIX + (size_t)((ly0 + k) * B + lx);
                 T[k] = sl.tout[s];
-                S0[k] = sl.c0[s]; S1[k] = sl.c1[s]; S2[k] = sl.c2[s];
+                gS[k] = g0[k] * sl.c0[s] + g1[k] * sl.c1[s] + g2[k] * sl.c2[s];
             } else {
                 T[k] = Tfin[it.poff + pix];
-                S0[k] = T[k] * bg0; S1[k] = T[k] * bg1; S2[k] = T[k] * bg2;  // colour behind the last entry
+                gS[k] = T[k] * (g0[k] * bg0 + g1[k] * bg1 + g2[k] * bg2);  // behind the last entry: T bg
             }
         }
         mylast = max(mylast, lastp[k]);
@@ -689,6 +692,13 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
     // never walk past the item's own entries, whatever `last` holds
     const int top = min(s_n, hi);
     const int lane = threadIdx.x & 31;
+    // this lane's partial gradient of the current entry: du, dv, dA, dB, dC,
+    // d opacity, d r, d g, d b.  With one pixel per thread each blending lane
+    // assigns all nine (no per-entry zeroing; lanes that did not blend are
+    // masked at the reduction); with several pixels they accumulate from zero.
+    float vd[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) vd[i] = 0.f;
     for (int base = top > lo ? lo + ((top - lo - 1) / NT) * NT : lo - 1; base >= lo; base -= NT) {
         const int j = base + (int)threadIdx.x;
         bool keep = false;
@@ -730,7 +740,10 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
             const float cr = col.x, cg = col.y, cb = col.z;
             const float dx = a.x - pxc;
             const float adx = a.z * dx;
-            float du = 0.f, dv = 0.f, dA = 0.f, dB = 0.f, dC = 0.f, dop = 0.f, dr = 0.f, dgc = 0.f, db = 0.f;
+            if (PPT > 1) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) vd[i] = 0.f;
+            }
             bool any = false;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
@@ -743,30 +756,24 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                         const float raw = ex2_approx(e);
                         const float alpha = fminf(kAlphaMax, raw);
                         const float4 kc = s_k[kk];  // A, B, C, 1/o
-                        const float G = raw * kc.w;  // exp(power) = d alpha / d o
                         any = true;
                         // hardware reciprocal (about 1 ulp; 1 - alpha is in [0.01, 1]): the
                         // exactly rounded one costs a measured 6% of the kernel
                         const float inv = __fdividef(1.f, 1.f - alpha);
                         T[k] *= inv;  // transmittance in front of this entry
                         const float wT = alpha * T[k];
-                        dr += wT * g0[k];
-                        dgc += wT * g1[k];
-                        db += wT * g2[k];
-                        const float dLda = g0[k] * (T[k] * cr - S0[k] * inv) + g1[k] * (T[k] * cg - S1[k] * inv) +
-                                           g2[k] * (T[k] * cb - S2[k] * inv);
-                        S0[k] += wT * cr;
-                        S1[k] += wT * cg;
-                        S2[k] += wT * cb;
-                        if (raw <= kAlphaMax) {
-                            dop += dLda * G;
-                            const float dp = dLda * alpha;
-                            du -= dp * (kc.x * dx + kc.y * dy);
-                            dv -= dp * (kc.y * dx + kc.z * dy);
-                            dA -= 0.5f * dp * dx * dx;
-                            dB -= dp * dx * dy;
-                            dC -= 0.5f * dp * dy * dy;
-                        }
+                        const float gcol = fmaf(g0[k], cr, fmaf(g1[k], cg, g2[k] * cb));
+                        const float dLda = fmaf(T[k], gcol, -gS[k] * inv);
+                        gS[k] = fmaf(wT, gcol, gS[k]);
+                        // below the clamp: d alpha / d o = exp(power), d alpha / d power = alpha
+                        const float dp = raw <= kAlphaMax ? dLda * alpha : 0.f;
+                        const float dopa = raw <= kAlphaMax ? dLda * raw * kc.w : 0.f;
+                        const float qx = dp * dx, qy = dp * dy;
+                        const float v[9] = {-fmaf(kc.x, qx, kc.y * qy), -fmaf(kc.y, qx, kc.z * qy),
+                                            -0.5f * qx * dx, -qx * dy, -0.5f * qy * dy, dopa,
+                                            wT * g0[k], wT * g1[k], wT * g2[k]};
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) vd[i] = PPT == 1 ? v[i] : vd[i] + v[i];
                     }
                 }
             }
@@ -777,13 +784,15 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                 // vector atomics) instead of the 12-shuffle warp reduction
                 if (any) {
                     float4* gp = grad2d + 3 * (size_t)s_g[kk];
-                    atomicAdd(gp, make_float4(du, dv, dA, dB));
-                    atomicAdd(gp + 1, make_float4(dC, dop, dr, dgc));
-                    atomicAdd((float*)(gp + 2), db);
+                    atomicAdd(gp, make_float4(vd[0], vd[1], vd[2], vd[3]));
+                    atomicAdd(gp + 1, make_float4(vd[4], vd[5], vd[6], vd[7]));
+                    atomicAdd((float*)(gp + 2), vd[8]);
                 }
                 continue;
             }
-            const float vals[9] = {du, dv, dA, dB, dC, dop, dr, dgc, db};
+            float vals[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) vals[i] = any ? vd[i] : 0.f;
             int idx;
             const float tot = warp_sum9(vals, lane, &idx);
             if (idx >= 0) atomicAdd((float*)(grad2d + 3 * (size_t)s_g[kk]) + idx, tot);
