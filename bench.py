@@ -34,8 +34,13 @@ sys.path.insert(0, ROOT)
 W_FULL, H_FULL = 1237, 822
 N_GAUSS = 2_000_000
 N_VIEWS = 16
-FLOPS_FWD = 22     # FP32 flops per blended (pixel, Gaussian) entry, forward
-FLOPS_BWD = 58     # FP32 flops per blended entry, backward (every blended entry is revisited)
+# Algorithmic FP32 work of the compositing passes (Eq. 1 and its adjoint), per
+# (pixel, list entry): every entry a pixel examines needs its alpha test --
+# offsets, quadratic form, exponential, clamp, threshold; a blended entry adds
+# the transmittance and colour update (forward) or the gradient (backward).
+FLOPS_TEST = 12
+FLOPS_FWD_BLEND = 7
+FLOPS_BWD_BLEND = 38
 SM_COUNT, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
 
 
@@ -51,11 +56,52 @@ def parse():
                     help="render-side record storage (mixed: float16 conic/opacity, bfloat16 colour)")
     ap.add_argument("--graph", action="store_true",
                     help="also time the step captured as one CUDA graph (graph_ms_per_view)")
-    ap.add_argument("--fused-adam", action="store_true",
-                    help="projection adjoint fused with Adam (default: two kernels)")
+    ap.add_argument("--shape", default=None,
+                    help="render launch shape, e.g. t8f1b1s0 (tile, pixels per thread fwd/bwd, split); "
+                         "default: autotuned over the candidates")
+    ap.add_argument("--separate-adam", action="store_true",
+                    help="projection adjoint and Adam as two kernels (default: one fused kernel)")
     ap.add_argument("--cpu-frac", type=float, default=0.125,
                     help="area/Gaussian fraction of one view timed for the CPU baseline")
     return ap.parse_args()
+
+
+def parse_shape(label: str):
+    """Shape from its label t<tile>f<ppt fwd>b<ppt bwd>s<split>."""
+    import re
+    from paper_2503_18402_gb300.autotune import Shape
+    mt = re.fullmatch(r"t(\d+)f(\d+)b(\d+)s(-?\d+)", label)
+    if not mt:
+        raise SystemExit(f"bad --shape {label!r}: want e.g. t8f1b1s0")
+    return Shape(*(int(x) for x in mt.groups()))
+
+
+# source file of each timed stage's kernels (for the ncu summaries' hash check)
+STAGE_SOURCE = {"render_fwd": "render.cu", "render_bwd": "render.cu", "project": "project.cu",
+                "project_bwd": "project.cu", "project_bwd_adam": "project.cu", "adam": "optim.cu"}
+
+
+def measured_traffic(stage: str):
+    """DRAM bytes per launch of the stage's kernel from a committed ncu summary
+    under profiles/ (lines 'stage:', 'source_sha1:', 'dram_bytes_per_launch:'),
+    or None when there is none or it was taken on another version of the
+    kernel's source file."""
+    import glob
+    import hashlib
+    src = STAGE_SOURCE.get(stage)
+    if src is None:
+        return None
+    with open(os.path.join(ROOT, "paper_2503_18402_gb300", "csrc", src), "rb") as f:
+        sha = hashlib.sha1(f.read()).hexdigest()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith((" ", "|", "#")):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("stage") == stage and kv.get("source_sha1") == sha and "dram_bytes_per_launch" in kv:
+            return int(kv["dram_bytes_per_launch"])
+    return None
 
 
 def config(args, n_gauss, shape=None):
@@ -65,7 +111,7 @@ def config(args, n_gauss, shape=None):
             "tile": shape.tile if shape else 16, "render_shape": shape.label() if shape else None,
             "sh_degree": 3, "loss": "0.8 L1 + 0.2 D-SSIM",
             "step": "project+bin+render_fwd+loss+render_bwd+project_bwd+adam",
-            "adjoint_adam": "fused" if args.fused_adam else "two kernels",
+            "adjoint_adam": "two kernels" if args.separate_adam else "fused",
             "render_records": "mixed fp16/bf16" if args.record == "mixed" else "fp32",
             "l2": "working set 1.9 GB > L2 (no flush)", "parallelism": f"replicas{args.gpus}"}
 
@@ -193,7 +239,7 @@ def run_ours(args):
             mark("loss")
         r.backward_render(fr, dL, stream)
         adam_t[0] += 1
-        if not args.fused_adam:
+        if args.separate_adam:
             capi.dg_project_bwd(params, stride, P, gcams[j], 1, r.opts, r.radius, r.clamp, r.grad2d, grads, stream)
             if mark:
                 mark("project_bwd")
@@ -207,7 +253,7 @@ def run_ours(args):
     # launch-shape autotuning: time each candidate on a few steps, keep the fastest
     tuner = RenderTuner(dev, opts)
     tune_ms = {}
-    for shape in CANDIDATES:
+    for shape in ([parse_shape(args.shape)] if args.shape else CANDIDATES):
         r = tuner.rasterizer(shape)
         for i in range(2):
             step_with(r, i)
@@ -225,11 +271,13 @@ def run_ours(args):
     params.copy_(torch.from_numpy(np.ascontiguousarray(model.T)).to(dev))
     m.zero_(); v.zero_(); adam_t[0] = 0
 
-    # algorithmic work per view: examined entries (forward) and back-traversed entries
-    E_f, E_b, M_tot = [], [], []
+    # algorithmic work per view: entries examined by the forward, entries the
+    # backward walks (up to each pixel's last blended one), blended entries
+    E_f, E_l, E_b, M_tot = [], [], [], []
     for c in gcams:
         fr = rz.forward(params, P, c, examined=True)
         E_f.append(int(rz.examined.sum().item()))
+        E_l.append(int(fr.last.sum().item()))
         E_b.append(int(rz.blended.sum().item()))
         M_tot.append(fr.M)
 
@@ -291,7 +339,7 @@ def run_ours(args):
         fr0 = gr.forward(params, P, gcams[0])
         M_cap = int(max(M_tot) * 1.25) + 4096
         sg = StepGraph(dev, gr.opts, gshape.ppt_fwd, gshape.ppt_bwd, params, m, v, grads, stride, P, [gcams[0]],
-                       M_cap, 0.2)
+                       M_cap, 0.2, fused=not args.separate_adam)
         adam_t[0] += 1
         sg.capture([gcams[0]], capi.dg_adam_hparams_fill(lr, 0.9, 0.999, 1e-15, adam_t[0]), [targets[0]])
         for i in range(args.warmup):
@@ -348,8 +396,10 @@ def run_ours(args):
     stages = {k: {"ms": round(v / args.steps, 4), "share": round(v / tot, 4)} for k, v in stage_ms.items()}
     out["stages"] = stages
     pf = sum(E_f) / len(E_f)
+    pl = sum(E_l) / len(E_l)
     pb = sum(E_b) / len(E_b)
-    work = {"render_fwd": ("alu", pb * FLOPS_FWD), "render_bwd": ("alu", pb * FLOPS_BWD),
+    work = {"render_fwd": ("alu", pf * FLOPS_TEST + pb * FLOPS_FWD_BLEND),
+            "render_bwd": ("alu", pl * FLOPS_TEST + pb * FLOPS_BWD_BLEND),
             "project": ("hbm", P * 297.0), "project_bwd": ("hbm", P * 525.0), "adam": ("hbm", P * 1652.0),
             "project_bwd_adam": ("hbm", P * 1469.0)}
     dom = max((k for k in stages if k in work), key=lambda k: stages[k]["ms"])
@@ -364,18 +414,20 @@ def run_ours(args):
         peak = SM_COUNT * FP32_LANES * 2 * MAX_MHZ * 1e6 / 1e12
         ach = units / dur_s / 1e12
         out["roofline"] = {"bound": "alu", "kernel": dom, "achieved": round(ach, 3), "peak": round(peak, 2),
-                           "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                           "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": measured_traffic(dom),
                            "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
     else:
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         ach = units / dur_s / 1e9
         out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                           "frac": round(ach / hbm, 4), "traffic": None,
+                           "frac": round(ach / hbm, 4), "traffic": measured_traffic(dom),
                            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s"}
     out["work"] = {"pairs_per_view": int(sum(M_tot) / len(M_tot)), "examined_per_view": int(pf),
-                   "blended_per_view": int(pb)}
+                   "walked_back_per_view": int(pl), "blended_per_view": int(pb)}
+    # the rasterizer's forward and backward: projection, binning, both compositing passes
     out["fwd_bwd_ms_per_view"] = round(sum(stages[k]["ms"] for k in stages
-                                           if k not in ("adam", "loss", "project_bwd_adam")), 4)
+                                           if k in ("project", "bin_count", "host_sync", "bin_sort", "render_fwd",
+                                                    "render_bwd")), 4)
     out["e2e"] = {"value": round(e2e_ms / views_total, 4), "unit": "ms/view",
                   "h2d_bytes_per_step": int(targets[0].numel() * 4), "d2h_bytes_per_step": 4 + 8}
     out["gpu_launches"] = int(launches)

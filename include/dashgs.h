@@ -355,6 +355,18 @@ DG_API dg_status dg_adam_step_dev(float* params, const float* grads, float* m, f
                                   int64_t P, const dg_adam_hparams* hp_dev, const int32_t* skip_if,
                                   dg_stream stream);
 
+/* dg_project_bwd_adam with the hyper-parameters read from device memory when
+ * the kernel runs (hp_dev: one dg_adam_hparams, e.g. filled by
+ * dg_adam_hparams_fill and copied) and the update skipped when *skip_if != 0
+ * (skip_if: nullable device int32, e.g. dg_bin_sort's status), for a step
+ * captured once in a CUDA graph and replayed (cf. dg_adam_step_dev).  The
+ * adjoint (and grads, when given) is computed either way. */
+DG_API dg_status dg_project_bwd_adam_dev(float* params, int64_t stride, int64_t P, const dg_camera* cams,
+                                         const dg_camera* cams_dev, int32_t n_views, const dg_raster_opts* opts,
+                                         const int32_t* radius, const uint8_t* clamp, const float* grad2d,
+                                         float* grads, float* m, float* v, const dg_adam_hparams* hp_dev,
+                                         const int32_t* skip_if, dg_stream stream);
+
 /* ---------------------------------------------------------------------- */
 /* Scheduled densification (supplementary "Densification of DashGaussian"):
  * prune first (N'), then clone or split the Gaussians that meet the 3DGS

@@ -25,6 +25,7 @@ DG_OK, DG_ERR_ARG, DG_ERR_CAPACITY, DG_ERR_TIMEOUT, DG_ERR_CUDA = 0, -1, -2, -3,
 MAX_VIEWS = 16
 EXPORTS = ("dg_last_error", "dg_abi_version", "dg_kernel_launches", "dg_project", "dg_bin_workspace_size", "dg_bin_count",
            "dg_bin_sort", "dg_render_workspace_size", "dg_render_fwd", "dg_render_bwd", "dg_pack_records", "dg_project_bwd", "dg_project_bwd_adam",
+           "dg_project_bwd_adam_dev",
            "dg_loss_workspace_size", "dg_ssim_workspace_size", "dg_loss_l1_dssim",
            "dg_loss_l1", "dg_loss_l1_noalloc", "dg_adam_step", "dg_adam_hparams_fill", "dg_adam_step_dev",
            "dg_sparse_adam_step", "dg_visibility", "dg_spectrum_workspace_size",
@@ -135,6 +136,7 @@ _SIGS = {
     "dg_project_bwd": ([_P, _I64, _I64, _CAM, _P, _I32, _OPT, _P, _P, _P, _P, _P], _ST),
     "dg_project_bwd_adam": ([_P, _I64, _I64, _CAM, _P, _I32, _OPT, _P, _P, _P, _P, _P, _P, _P, ctypes.c_float,
                              ctypes.c_float, ctypes.c_float, _I64, _P], _ST),
+    "dg_project_bwd_adam_dev": ([_P, _I64, _I64, _CAM, _P, _I32, _OPT, _P, _P, _P, _P, _P, _P, _P, _P, _P], _ST),
     "dg_ssim_workspace_size": ([_P, _I32], _SZ),
     "dg_loss_l1_dssim": ([_P, _P, _P, _I32, ctypes.c_float, _P, _P, _P, _SZ, _P], _ST),
     "dg_loss_workspace_size": ([_I64], _SZ),
@@ -274,6 +276,13 @@ def dg_project_bwd_adam(params, stride, P, cams, n_views, opts, radius, clamp, g
     _check(_lib.dg_project_bwd_adam(_a(params), stride, P, _c(cams), _a(cams_dev), n_views, ctypes.byref(opts),
                                     _a(radius), _a(clamp), _a(grad2d), _a(grads), _a(m), _a(v),
                                     ctypes.cast(lr_arr, ctypes.c_void_p), beta1, beta2, eps, step, _s(stream)))
+
+
+def dg_project_bwd_adam_dev(params, stride, P, cams, n_views, opts, radius, clamp, grad2d, grads, m, v, hp_dev,
+                            skip_if=None, stream=None, cams_dev=None):
+    _check(_lib.dg_project_bwd_adam_dev(_a(params), stride, P, _c(cams), _a(cams_dev), n_views, ctypes.byref(opts),
+                                        _a(radius), _a(clamp), _a(grad2d), _a(grads), _a(m), _a(v), _a(hp_dev),
+                                        _a(skip_if), _s(stream)))
 
 
 def dg_loss_workspace_size(n) -> int:

@@ -293,10 +293,18 @@ __global__ void __launch_bounds__(128, 4)
 k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host, const dg_camera* cdev,
               float near_plane, float eps2d, float mip2d, const int* __restrict__ radius, const uint8_t* __restrict__ clampm,
               const float4* __restrict__ grad2d, float* __restrict__ grads, float* __restrict__ am,
-              float* __restrict__ av, AdamHp hp)
+              float* __restrict__ av, AdamHp hp_val, const AdamHp* __restrict__ hp_dev,
+              const int* __restrict__ skip_if)
 {
     __shared__ ViewSet s_vs;
     __shared__ float s_g[ADAM ? DG_NPARAM : 1][128];  // ADAM: this CTA's gradients, for the row sweep
+    __shared__ AdamHp s_hp;                            // ADAM: this step's hyper-parameters
+    if (ADAM) {
+        // from device memory when given (a captured step reads the values of the replay)
+        const float* src = (const float*)(hp_dev ? hp_dev : &hp_val);
+        for (int k = threadIdx.x; k < (int)(sizeof(AdamHp) / sizeof(float)); k += blockDim.x)
+            ((float*)&s_hp)[k] = src[k];
+    }
     const ViewSet& vs = block_views(vs_host, cdev, &s_vs);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     auto put = [&](int row, float gval) {
@@ -464,18 +472,37 @@ k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host,
     };
     if (i < P) adjoint();
     if (ADAM) {
-        // Adam over the CTA's [59][128] tile: one coalesced row at a time, every
-        // row's loads independent of the previous row's update
+        // Adam over the CTA's [59][128] tile, coalesced rows, RB rows at a time:
+        // all 3 RB loads of a group are issued before its first store (the
+        // compiler cannot move loads of later rows above stores to earlier
+        // ones, so a row-at-a-time loop keeps only one row's loads in flight)
+        constexpr int RB = 16;
         __syncthreads();
-        if (i < P) {
-#pragma unroll 4
-            for (int r = 0; r < DG_NPARAM; ++r) {
-                const long long o = (long long)r * stride + i;
-                float p = prm[o], mm = am[o], vv = av[o];
-                adam_update(p, mm, vv, s_g[r][threadIdx.x], adam_row(hp.lr[r], hp), hp);
-                prm[o] = p;
-                am[o] = mm;
-                av[o] = vv;
+        const AdamHp& hp = s_hp;
+        // (skip_if: e.g. the step's pair list overflowed; then no update)
+        if (i < P && !(skip_if && *skip_if != 0)) {
+            for (int r0 = 0; r0 < DG_NPARAM; r0 += RB) {
+                float p[RB], mm[RB], vv[RB];
+#pragma unroll
+                for (int j = 0; j < RB; ++j) {
+                    if (r0 + j < DG_NPARAM) {
+                        const long long o = (long long)(r0 + j) * stride + i;
+                        p[j] = prm[o];
+                        mm[j] = am[o];
+                        vv[j] = av[o];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < RB; ++j) {
+                    if (r0 + j < DG_NPARAM) {
+                        const int r = r0 + j;
+                        adam_update(p[j], mm[j], vv[j], s_g[r][threadIdx.x], adam_row(hp.lr[r], hp), hp);
+                        const long long o = (long long)r * stride + i;
+                        prm[o] = p[j];
+                        am[o] = mm[j];
+                        av[o] = vv[j];
+                    }
+                }
             }
         }
     }
@@ -549,14 +576,14 @@ template <bool ADAM, bool SINGLE>
 static void launch_project_bwd(int nb, int blocks, int threads, cudaStream_t s, float* params, long long st, int P,
                                const dg::ViewSet& vs, const dg_camera* cams_dev, const dg_raster_opts* opts,
                                const int32_t* radius, const uint8_t* clamp, const float4* g2, float* grads, float* m,
-                               float* v, const dg::AdamHp& hp)
+                               float* v, const dg::AdamHp& hp, const dg::AdamHp* hp_dev, const int* skip_if)
 {
     const float np = opts->near_plane, e2 = opts->eps2d, mp = opts->mip2d;
     switch (nb) {
-    case 1: dg::k_project_bwd<1, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, mp, radius, clamp, g2, grads, m, v, hp); break;
-    case 4: dg::k_project_bwd<4, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, mp, radius, clamp, g2, grads, m, v, hp); break;
-    case 9: dg::k_project_bwd<9, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, mp, radius, clamp, g2, grads, m, v, hp); break;
-    default: dg::k_project_bwd<16, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, mp, radius, clamp, g2, grads, m, v, hp); break;
+    case 1: dg::k_project_bwd<1, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, mp, radius, clamp, g2, grads, m, v, hp, hp_dev, skip_if); break;
+    case 4: dg::k_project_bwd<4, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, mp, radius, clamp, g2, grads, m, v, hp, hp_dev, skip_if); break;
+    case 9: dg::k_project_bwd<9, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, mp, radius, clamp, g2, grads, m, v, hp, hp_dev, skip_if); break;
+    default: dg::k_project_bwd<16, ADAM, SINGLE><<<blocks, threads, 0, s>>>(params, st, P, vs, cams_dev, np, e2, mp, radius, clamp, g2, grads, m, v, hp, hp_dev, skip_if); break;
     }
 }
 
@@ -565,7 +592,7 @@ static dg_status project_bwd(float* params, int64_t stride, int64_t P, const dg_
                              const dg_camera* cams_dev, int32_t n_views,
                              const dg_raster_opts* opts, const int32_t* radius, const uint8_t* clamp,
                              const float* grad2d, float* grads, float* m, float* v, const dg::AdamHp& hp,
-                             dg_stream stream)
+                             const dg::AdamHp* hp_dev, const int* skip_if, dg_stream stream)
 {
     if (!dg_check_cameras(cams, n_views) || !check_opts(opts)) return DG_ERR_ARG;
     if (P < 0 || P > INT32_MAX || stride < P || (long long)P * n_views > (long long)UINT32_MAX) {
@@ -585,8 +612,8 @@ static dg_status project_bwd(float* params, int64_t stride, int64_t P, const dg_
     const long long st = (long long)stride;
     const float4* g2 = (const float4*)grad2d;
     const int nb = opts->sh_degree == 0 ? 1 : opts->sh_degree == 1 ? 4 : opts->sh_degree == 2 ? 9 : 16;
-    if (n_views == 1) launch_project_bwd<ADAM, true>(nb, blocks, threads, s, params, st, (int)P, vs, cams_dev, opts, radius, clamp, g2, grads, m, v, hp);
-    else launch_project_bwd<ADAM, false>(nb, blocks, threads, s, params, st, (int)P, vs, cams_dev, opts, radius, clamp, g2, grads, m, v, hp);
+    if (n_views == 1) launch_project_bwd<ADAM, true>(nb, blocks, threads, s, params, st, (int)P, vs, cams_dev, opts, radius, clamp, g2, grads, m, v, hp, hp_dev, skip_if);
+    else launch_project_bwd<ADAM, false>(nb, blocks, threads, s, params, st, (int)P, vs, cams_dev, opts, radius, clamp, g2, grads, m, v, hp, hp_dev, skip_if);
     dg_note_launch();
     return dg_check_launch(ADAM ? "project_bwd_adam" : "project_bwd");
 }
@@ -598,7 +625,7 @@ extern "C" dg_status dg_project_bwd(const float* params, int64_t stride, int64_t
 {
     // the non-Adam instantiation never writes params
     return project_bwd<false>(const_cast<float*>(params), stride, P, cams, cams_dev, n_views, opts, radius, clamp,
-                              grad2d, grads, nullptr, nullptr, dg::AdamHp{}, stream);
+                              grad2d, grads, nullptr, nullptr, dg::AdamHp{}, nullptr, nullptr, stream);
 }
 
 extern "C" dg_status dg_project_bwd_adam(float* params, int64_t stride, int64_t P, const dg_camera* cams,
@@ -609,5 +636,16 @@ extern "C" dg_status dg_project_bwd_adam(float* params, int64_t stride, int64_t 
 {
     if (step < 1 || !lr) { dg_set_error("step must be >= 1 and lr given"); return DG_ERR_ARG; }
     return project_bwd<true>(params, stride, P, cams, cams_dev, n_views, opts, radius, clamp, grad2d, grads, m, v,
-                             dg_adam_hp(lr, beta1, beta2, eps, step), stream);
+                             dg_adam_hp(lr, beta1, beta2, eps, step), nullptr, nullptr, stream);
+}
+
+extern "C" dg_status dg_project_bwd_adam_dev(float* params, int64_t stride, int64_t P, const dg_camera* cams,
+                                             const dg_camera* cams_dev, int32_t n_views, const dg_raster_opts* opts,
+                                             const int32_t* radius, const uint8_t* clamp, const float* grad2d,
+                                             float* grads, float* m, float* v, const dg_adam_hparams* hp_dev,
+                                             const int32_t* skip_if, dg_stream stream)
+{
+    if (!hp_dev) { dg_set_error("hp_dev is null"); return DG_ERR_ARG; }
+    return project_bwd<true>(params, stride, P, cams, cams_dev, n_views, opts, radius, clamp, grad2d, grads, m, v,
+                             dg::AdamHp{}, hp_dev, skip_if, stream);
 }

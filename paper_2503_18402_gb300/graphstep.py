@@ -10,9 +10,10 @@ they run: the cameras (``cams_dev``, read by the projection and its adjoint),
 the Adam hyper-parameters (``hp_dev``: position learning rate and step
 count), and the targets (copied into the graph's target buffer before the
 launch).  What is fixed in a graph: the Gaussian count P, the image sizes,
-the launch shape and the pair capacity M_cap.  The binning writes a device
-status word when a step needs more than M_cap pairs; Adam then skips its
-update (dg_adam_step_dev's skip flag), and the caller, which reads the status
+the launch shape and the pair capacity M_cap.  The projection adjoint and
+Adam run as one kernel (dg_project_bwd_adam_dev) unless ``fused`` is off.
+The binning writes a device status word when a step needs more than M_cap
+pairs; Adam then skips its update (the skip flag), and the caller, which reads the status
 and the pair count asynchronously after the replay, re-captures with a
 larger capacity and repeats the step.
 """
@@ -29,10 +30,11 @@ from .raster import Rasterizer
 
 class StepGraph:
     def __init__(self, device, opts: capi.RasterOpts, ppt_fwd, ppt_bwd, params, m, v, grads, stride: int, P: int,
-                 cams, M_cap: int, ssim_lambda: float, stats=None):
-        """params/m/v/grads: planar [59][stride] buffers (fixed addresses);
-        cams: host cameras of the batch (their sizes fix the graph); stats:
-        (acc, den, maxr) densification accumulators, or None."""
+                 cams, M_cap: int, ssim_lambda: float, stats=None, fused: bool = True):
+        """params/m/v/grads: planar [59][stride] buffers (fixed addresses;
+        grads is unused when fused); cams: host cameras of the batch (their
+        sizes fix the graph); stats: (acc, den, maxr) densification
+        accumulators, or None."""
         self.device = torch.device(device)
         self.P = P
         self.V = len(cams)
@@ -64,6 +66,7 @@ class StepGraph:
         self.params, self.m, self.v, self.grads, self.stride = params, m, v, grads, stride
         self.lam = ssim_lambda
         self.stats = stats
+        self.fused = fused
         self.graph = None
 
     def _sequence(self, stream):
@@ -77,6 +80,11 @@ class StepGraph:
         if self.stats is not None:
             acc, den, maxr = self.stats
             capi.dg_densify_stats(rz.grad2d, rz.radius, self.P, carr, self.V, acc, den, maxr, stream)
+        if self.fused:
+            capi.dg_project_bwd_adam_dev(self.params, self.stride, self.P, carr, self.V, rz.opts, rz.radius, rz.clamp,
+                                         rz.grad2d, None, self.m, self.v, self.hp_dev, skip_if=rz.status,
+                                         stream=stream, cams_dev=self.cams_dev)
+            return
         capi.dg_project_bwd(prm, self.stride, self.P, carr, self.V, rz.opts, rz.radius, rz.clamp, rz.grad2d,
                             self.grads[:, : self.P], stream, cams_dev=self.cams_dev)
         capi.dg_adam_step_dev(self.params, self.grads, self.m, self.v, self.stride, self.P, self.hp_dev,

@@ -80,7 +80,12 @@ def test_adam_from_device_hparams_and_skip_flag():
     assert float(c[1].abs().max()) == 0.0
 
 
-def test_captured_step_replays_the_direct_sequence():
+@pytest.mark.parametrize("fused", [False, True])
+def test_captured_step_replays_the_direct_sequence(fused):
+    """The captured step (projection adjoint and Adam as two kernels, or
+    fused) equals the direct sequence of calls.  Fused, the gradient is not
+    stored; it is read from the first moment, which after step 1 from zero
+    moments is (1 - beta1) g."""
     g, cams = _scene(3000, 5)
     P, V = g.shape[0], len(cams)
     stride = P + 7
@@ -109,14 +114,18 @@ def test_captured_step_replays_the_direct_sequence():
     # the same inputs from the same start
     params2 = torch.from_numpy(base.copy()).cuda()
     m2, v2, grads2 = torch.zeros_like(params2), torch.zeros_like(params2), torch.zeros_like(params2)
-    sg = StepGraph("cuda", capi.raster_opts(tile=8), 1, 1, params2, m2, v2, grads2, stride, P, cams, fr.M + 100, 0.2)
+    sg = StepGraph("cuda", capi.raster_opts(tile=8), 1, 1, params2, m2, v2, grads2, stride, P, cams, fr.M + 100, 0.2,
+                   fused=fused)
+
+    def step_grad():
+        return G.np_(m2[:, :P]) / np.float32(0.1) if fused else G.np_(grads2[:, :P])
     hp1 = capi.dg_adam_hparams_fill(lr, 0.9, 0.999, 1e-15, 1)
     sg.capture(cams, hp1, targets)
     status, M = sg.result()
     assert status == 0 and M == fr.M
     np.testing.assert_array_equal(G.np_(sg.rz.fixed["img"]), img_direct)
     np.testing.assert_allclose(G.np_(sg.loss), G.np_(loss), rtol=0, atol=1e-7)
-    ok, worst, nbad = G.grad_close(G.np_(grads2[:, :P]), G.np_(grads[:, :P]))
+    ok, worst, nbad = G.grad_close(step_grad(), G.np_(grads[:, :P]))
     assert ok, (worst, nbad)
     # replay with the step-1 state restored: same result again
     params2.copy_(torch.from_numpy(base.copy()).cuda()); m2.zero_(); v2.zero_()
@@ -124,7 +133,7 @@ def test_captured_step_replays_the_direct_sequence():
     status, M = sg.result()
     assert status == 0
     np.testing.assert_array_equal(G.np_(sg.rz.fixed["img"]), img_direct)
-    ok, worst, nbad = G.grad_close(G.np_(grads2[:, :P]), G.np_(grads[:, :P]))
+    ok, worst, nbad = G.grad_close(step_grad(), G.np_(grads[:, :P]))
     assert ok, (worst, nbad)
     # new cameras through the same graph: equals a direct render of them
     cams_b = [G.gpu_camera(synth.camera_cfg0(c.width, c.height, 3.5 + 0.4 * i)) for i, c in enumerate(cams)]

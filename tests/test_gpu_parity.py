@@ -490,6 +490,54 @@ def test_fused_project_bwd_adam_matches_two_calls(sh, V):
     np.testing.assert_array_equal(G.np_(p3), G.np_(p2))
 
 
+def test_fused_project_bwd_adam_device_hparams_and_skip():
+    """dg_project_bwd_adam_dev (hyper-parameters read from device memory, as a
+    replayed CUDA graph does) gives the bits of dg_project_bwd_adam with the
+    same values; with the skip word set it leaves params, m and v untouched
+    and still writes the gradient."""
+    import ctypes
+    g = synth.random_gaussians(2000, 77)
+    g[:, 3:6] += 0.3
+    cams = [G.gpu_camera(synth.camera_cfg0(64, 64, 4.0))]
+    opts = capi.raster_opts(sh_degree=3)
+    rz = Rasterizer("cuda", opts)
+    P = g.shape[0]
+    stride = P + 5
+    base = np.zeros((59, stride), np.float32)
+    base[:, :P] = g.T
+    params = torch.from_numpy(base).cuda()
+    fr = rz.forward(params[:, :P], P, cams)
+    rng = np.random.default_rng(3)
+    dL = torch.from_numpy((rng.normal(size=fr.flat_img.numel()) / 1e4).astype(np.float32)).cuda()
+    rz.backward(params[:, :P], fr, dL, torch.empty_like(params[:, :P]))
+    lr = np.linspace(1e-4, 1e-2, 59).astype(np.float32)
+    m0 = torch.from_numpy(rng.normal(size=(59, stride)).astype(np.float32) * 1e-3).cuda()
+    v0 = torch.from_numpy(np.abs(rng.normal(size=(59, stride))).astype(np.float32) * 1e-6).cuda()
+    p1, m1, v1 = params.clone(), m0.clone(), v0.clone()
+    capi.dg_project_bwd_adam(p1, stride, P, cams, 1, opts, rz.radius, rz.clamp, rz.grad2d, None, m1, v1, lr, 0.9,
+                             0.999, 1e-15, 9)
+    hp = capi.dg_adam_hparams_fill(lr, 0.9, 0.999, 1e-15, 9)
+    raw = np.frombuffer(ctypes.string_at(ctypes.addressof(hp), ctypes.sizeof(hp)), dtype=np.uint8).copy()
+    hp_dev = torch.from_numpy(raw).cuda()
+    p2, m2, v2 = params.clone(), m0.clone(), v0.clone()
+    capi.dg_project_bwd_adam_dev(p2, stride, P, cams, 1, opts, rz.radius, rz.clamp, rz.grad2d, None, m2, v2, hp_dev,
+                                 skip_if=torch.zeros(1, dtype=torch.int32, device="cuda"))
+    p3, m3, v3 = params.clone(), m0.clone(), v0.clone()
+    grads3 = torch.zeros_like(params)
+    capi.dg_project_bwd_adam_dev(p3, stride, P, cams, 1, opts, rz.radius, rz.clamp, rz.grad2d, grads3, m3, v3, hp_dev,
+                                 skip_if=torch.full((1,), -2, dtype=torch.int32, device="cuda"))
+    grads4 = torch.zeros_like(params)
+    capi.dg_project_bwd(params, stride, P, cams, 1, opts, rz.radius, rz.clamp, rz.grad2d, grads4)
+    torch.cuda.synchronize()
+    for a, b in ((p1, p2), (m1, m2), (v1, v2)):
+        np.testing.assert_array_equal(G.np_(a), G.np_(b))
+    for a, b in ((p3, params), (m3, m0), (v3, v0)):
+        np.testing.assert_array_equal(G.np_(a), G.np_(b))
+    assert float(grads3.abs().max()) > 0.0
+    ok, worst, nbad = G.grad_close(G.np_(grads3), G.np_(grads4))
+    assert ok, (worst, nbad)
+
+
 # ---------------------------------------------------------------- full size, sampled
 @pytest.fixture(scope="module")
 def fullsize():
