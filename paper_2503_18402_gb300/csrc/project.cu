@@ -286,11 +286,11 @@ k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs
 // form never stores or reloads the gradient.  Each thread owns one Gaussian
 // (one column of every row), so the in-place update races with nothing.
 // At most 128 registers (four 128-thread CTAs per SM), 96 when fused with
-// Adam (five CTAs, measured 0.664 -> 0.648 ms at 2M Gaussians; six were
+// Adam for one view (five CTAs, measured 0.664 -> 0.648 ms at 2M Gaussians; six were
 // slower): the adjoint streams 0.5-1.5 kB per Gaussian, and the extra resident
 // warps hide more memory latency than the few spilled values cost.
 template <int NB, bool ADAM, bool SINGLE>
-__global__ void __launch_bounds__(128, ADAM ? 5 : 4)
+__global__ void __launch_bounds__(128, ADAM && SINGLE ? 5 : 4)
 k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host, const dg_camera* cdev,
               float near_plane, float eps2d, float mip2d, const int* __restrict__ radius, const uint8_t* __restrict__ clampm,
               const float4* __restrict__ grad2d, float* __restrict__ grads, float* __restrict__ am,
