@@ -119,10 +119,10 @@ k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const ui
     const uint32_t n_tiles = (uint32_t)tg.off[tg.n];
     __shared__ int w_start[RS_TILE];      // pair offset of each staged Gaussian, relative to the block
     __shared__ uint32_t w_xy[RS_TILE];    // rect x0 | y0 << 16
-    __shared__ int w_wx[RS_TILE];         // rect width in tiles
+    __shared__ uint32_t w_wv[RS_TILE];    // rect width in tiles | view << 16
     __shared__ uint32_t w_g[RS_TILE];     // record index
-    __shared__ int w_base[RS_TILE];       // global tile id of the view's tile (0, 0)
-    __shared__ int w_tx[RS_TILE];         // tiles per row of the view
+    __shared__ int s_off[DG_MAX_VIEWS];   // global tile id of each view's tile (0, 0)
+    __shared__ int s_tx[DG_MAX_VIEWS];    // tiles per row of each view
     __shared__ uint32_t h[1 << RS_MAXBITS];
     const long long M = *M_dev;
     // a failed wait of the depth order (phase 1) is reported here
@@ -134,30 +134,53 @@ k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const ui
     // (status was cleared by the host before this launch; blocks only set errors)
     __shared__ int s_nw;
     for (int d = threadIdx.x; d < (1 << RS_MAXBITS); d += RS_THREADS) h[d] = 0;
+    for (int v = threadIdx.x; v < tg.n; v += RS_THREADS) {
+        s_off[v] = tg.off[v];
+        s_tx[v] = tg.TX[v];
+    }
     if (threadIdx.x == 0) s_nw = 0;
     __syncthreads();
     const long long base = (long long)blockIdx.x * RS_TILE;
     if (base < M) {  // block-uniform
         const long long end = (base + RS_TILE) < M ? (base + RS_TILE) : M;
         const int s_lo = bstart[blockIdx.x];
-        // stage the Gaussians whose pair range starts before `end` (a prefix of s_lo, s_lo+1, ...)
+        // stage the Gaussians whose pair range starts before `end` (a prefix of
+        // s_lo, s_lo + 1, ...).  Each link of the load chain (pair offset ->
+        // record index -> record) is issued for all of a thread's candidates at
+        // once; the second half of the candidates only when the block holds
+        // more than RS_TILE / 2 Gaussians (fewer than 4 pairs each).
+        constexpr int HALF = RS_IPT / 2;
+        long long st[RS_IPT];
+#pragma unroll
+        for (int k = 0; k < HALF; ++k) {
+            const long long s = (long long)s_lo + threadIdx.x + k * RS_THREADS;
+            st[k] = s < P ? (long long)poff[s] : LLONG_MAX;
+        }
+        const bool more = __syncthreads_or(st[HALF - 1] < end) != 0;
+#pragma unroll
+        for (int k = HALF; k < RS_IPT; ++k) {
+            const long long s = (long long)s_lo + threadIdx.x + k * RS_THREADS;
+            st[k] = more && s < P ? (long long)poff[s] : LLONG_MAX;
+        }
+        uint32_t gk[RS_IPT];
+#pragma unroll
+        for (int k = 0; k < RS_IPT; ++k)
+            gk[k] = st[k] < end ? order[(long long)s_lo + threadIdx.x + k * RS_THREADS] : 0u;
         int top = 0;
-        for (int w = threadIdx.x; w < RS_TILE; w += RS_THREADS) {
-            const long long s = (long long)s_lo + w;
-            if (s >= P) break;
-            const long long st = (long long)poff[s];
-            if (st >= end) break;
-            const uint32_t g = order[s];
-            const int v = (int)(g / Pv);
-            const float4 f0 = feat[3 * (size_t)g];
-            const Rect q = tile_rect(f0.x, f0.y, radius[g], B, tg.TX[v], tg.TY[v]);
-            w_start[w] = (int)(st - base);
-            w_xy[w] = (uint32_t)q.x0 | ((uint32_t)q.y0 << 16);
-            w_wx[w] = q.x1 - q.x0;
-            w_g[w] = g;
-            w_base[w] = tg.off[v];
-            w_tx[w] = tg.TX[v];
-            top = w + 1;
+#pragma unroll
+        for (int k = 0; k < RS_IPT; ++k) {
+            if (st[k] < end) {
+                const int w = (int)threadIdx.x + k * RS_THREADS;
+                const uint32_t g = gk[k];
+                const int v = (int)(g / Pv);
+                const float4 f0 = feat[3 * (size_t)g];
+                const Rect q = tile_rect(f0.x, f0.y, radius[g], B, tg.TX[v], tg.TY[v]);
+                w_start[w] = (int)(st[k] - base);
+                w_xy[w] = (uint32_t)q.x0 | ((uint32_t)q.y0 << 16);
+                w_wv[w] = (uint32_t)(q.x1 - q.x0) | ((uint32_t)v << 16);
+                w_g[w] = g;
+                top = w + 1;
+            }
         }
         if (top > 0) atomicMax(&s_nw, top);
         __syncthreads();
@@ -173,10 +196,11 @@ k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const ui
                 if (w_start[mid] <= rel0) lo = mid; else hi = mid - 1;
             }
             int j = rel0 - w_start[lo];
-            int wx = w_wx[lo];
+            uint32_t wv = w_wv[lo];
+            int wx = (int)(wv & 0xffffu);
             uint32_t xy = w_xy[lo];
             uint32_t g = w_g[lo];
-            int tb = w_base[lo], TXv = w_tx[lo];
+            int tb = s_off[wv >> 16], TXv = s_tx[wv >> 16];
             int next = lo + 1 < nw ? w_start[lo + 1] : nblock;
             int ry = j / wx, rx = j - ry * wx;
             uint32_t kk[RS_IPT], vv[RS_IPT];
@@ -186,8 +210,9 @@ k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const ui
                 if (e < cnt) {
                     if (rel0 + e >= next) {  // next Gaussian of the window
                         ++lo;
-                        wx = w_wx[lo]; xy = w_xy[lo]; g = w_g[lo];
-                        tb = w_base[lo]; TXv = w_tx[lo];
+                        wv = w_wv[lo];
+                        wx = (int)(wv & 0xffffu); xy = w_xy[lo]; g = w_g[lo];
+                        tb = s_off[wv >> 16]; TXv = s_tx[wv >> 16];
                         next = lo + 1 < nw ? w_start[lo + 1] : nblock;
                         rx = 0; ry = 0;
                     }
