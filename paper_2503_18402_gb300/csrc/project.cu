@@ -306,6 +306,7 @@ k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host,
     __shared__ ViewSet s_vs;
     __shared__ float s_g[ADAM ? DG_NPARAM : 1][128];  // ADAM: this CTA's gradients, for the row sweep
     __shared__ AdamHp s_hp;                            // ADAM: this step's hyper-parameters
+    __shared__ AdamRowK s_rk[ADAM ? DG_NPARAM : 1];    // ADAM: per-row step and 1 / sqrt(1 - b2^t)
     if (ADAM) {
         // from device memory when given (a captured step reads the values of the replay)
         const float* src = (const float*)(hp_dev ? hp_dev : &hp_val);
@@ -313,6 +314,11 @@ k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host,
             ((float*)&s_hp)[k] = src[k];
     }
     const ViewSet& vs = block_views(vs_host, cdev, &s_vs);
+    if (ADAM) {
+        __syncthreads();  // s_hp complete (block_views has no barrier without device cameras)
+        if (threadIdx.x < DG_NPARAM) s_rk[threadIdx.x] = adam_row(s_hp.lr[threadIdx.x], s_hp);
+        // (published by the barrier before the Adam sweep)
+    }
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     auto put = [&](int row, float gval) {
         if (grads) grads[(long long)row * stride + i] = gval;
@@ -503,7 +509,7 @@ k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host,
                 for (int j = 0; j < RB; ++j) {
                     if (r0 + j < DG_NPARAM) {
                         const int r = r0 + j;
-                        adam_update(p[j], mm[j], vv[j], s_g[r][threadIdx.x], adam_row(hp.lr[r], hp), hp);
+                        adam_update(p[j], mm[j], vv[j], s_g[r][threadIdx.x], s_rk[r], hp);
                         const long long o = (long long)r * stride + i;
                         prm[o] = p[j];
                         am[o] = mm[j];
