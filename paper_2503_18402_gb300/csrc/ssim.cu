@@ -31,7 +31,6 @@ constexpr int SS_T = 32;             // output tile edge
 constexpr int SS_R = 5;              // window radius
 constexpr int SS_E = SS_T + 2 * SS_R; // staged edge (42)
 constexpr int SS_THREADS = 256;      // 32 x 8
-constexpr int SS_ROWS = SS_T / 8;    // output rows per thread
 constexpr float kC1 = 0.01f * 0.01f;
 constexpr float kC2 = 0.03f * 0.03f;
 
@@ -65,15 +64,31 @@ __device__ inline Blk decode(const SViews& sv)
     return b;
 }
 
-// Stage plane[y0 - R .. y0 + T + R) x [x0 - R ..) into s (zero outside the image).
+// Stage plane[y0 - R .. y0 + T + R) x [x0 - R ..) into s (zero outside the image);
+// a thread's loads are all issued before its first shared store.
 __device__ inline void stage(const float* __restrict__ plane, int W, int H, int x0, int y0, float (*s)[SS_E + 1])
 {
-    for (int i = threadIdx.x; i < SS_E * SS_E; i += SS_THREADS) {
+    constexpr int N = (SS_E * SS_E + SS_THREADS - 1) / SS_THREADS;
+    float v[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const int i = threadIdx.x + k * SS_THREADS;
         const int r = i / SS_E, c = i % SS_E;
         const int y = y0 - SS_R + r, x = x0 - SS_R + c;
-        s[r][c] = (x >= 0 && x < W && y >= 0 && y < H) ? plane[(size_t)y * W + x] : 0.f;
+        v[k] = (i < SS_E * SS_E && x >= 0 && x < W && y >= 0 && y < H) ? plane[(size_t)y * W + x] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const int i = threadIdx.x + k * SS_THREADS;
+        if (i < SS_E * SS_E) s[i / SS_E][i % SS_E] = v[k];
     }
 }
+
+// Work split of the two window passes: the horizontal pass gives each thread
+// SS_SL adjacent outputs of one staged row (one load per input, reused by the
+// SS_SL sums), the vertical pass SS_SL adjacent output rows of one column.
+constexpr int SS_SL = 4;
+static_assert((SS_THREADS / 32) * SS_SL == SS_T && SS_T / SS_SL == 8, "vertical: one warp per SS_SL rows; horizontal: 8 groups per row");
 
 __global__ void __launch_bounds__(SS_THREADS)
 k_ssim_fwd(const float* __restrict__ img, const float* __restrict__ tgt, SViews sv, Win win,
@@ -88,38 +103,52 @@ k_ssim_fwd(const float* __restrict__ img, const float* __restrict__ tgt, SViews 
     stage(img + b.plane, b.W, b.H, x0, y0, sx);
     stage(tgt + b.plane, b.W, b.H, x0, y0, sy);
     __syncthreads();
-    for (int i = threadIdx.x; i < SS_E * SS_T; i += SS_THREADS) {
-        const int r = i / SS_T, c = i % SS_T;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+    // (lanes: 8 groups of SS_SL columns x 4 rows per warp; banks all distinct)
+    for (int it = threadIdx.x; it < SS_E * (SS_T / SS_SL); it += SS_THREADS) {
+        const int r = it / (SS_T / SS_SL), c0 = (it % (SS_T / SS_SL)) * SS_SL;
+        float xv[SS_SL + 2 * SS_R], yv[SS_SL + 2 * SS_R];
 #pragma unroll
-        for (int k = 0; k <= 2 * SS_R; ++k) {
-            const float xv = sx[r][c + k], yv = sy[r][c + k], w = win.w[k];
-            s0 = fmaf(w, xv, s0);
-            s1 = fmaf(w, yv, s1);
-            s2 = fmaf(w, xv * xv, s2);
-            s3 = fmaf(w, yv * yv, s3);
-            s4 = fmaf(w, xv * yv, s4);
+        for (int q = 0; q < SS_SL + 2 * SS_R; ++q) { xv[q] = sx[r][c0 + q]; yv[q] = sy[r][c0 + q]; }
+#pragma unroll
+        for (int o = 0; o < SS_SL; ++o) {
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+#pragma unroll
+            for (int k = 0; k <= 2 * SS_R; ++k) {
+                const float x = xv[o + k], y = yv[o + k], w = win.w[k];
+                s0 = fmaf(w, x, s0);
+                s1 = fmaf(w, y, s1);
+                s2 = fmaf(w, x * x, s2);
+                s3 = fmaf(w, y * y, s3);
+                s4 = fmaf(w, x * y, s4);
+            }
+            hs[0][r][c0 + o] = s0; hs[1][r][c0 + o] = s1; hs[2][r][c0 + o] = s2;
+            hs[3][r][c0 + o] = s3; hs[4][r][c0 + o] = s4;
         }
-        hs[0][r][c] = s0; hs[1][r][c] = s1; hs[2][r][c] = s2; hs[3][r][c] = s3; hs[4][r][c] = s4;
     }
     __syncthreads();
-    const int c = threadIdx.x & 31, r0 = threadIdx.x >> 5;
+    // vertical pass: lane = column, warp w = output rows SS_SL w .. SS_SL w + SS_SL - 1
+    const int c = threadIdx.x & 31, rb = (threadIdx.x >> 5) * SS_SL;
+    float st[5][SS_SL];  // window sums of the five statistics at this thread's outputs
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        float col[SS_SL + 2 * SS_R];
+#pragma unroll
+        for (int q = 0; q < SS_SL + 2 * SS_R; ++q) col[q] = hs[t][rb + q][c];
+#pragma unroll
+        for (int j = 0; j < SS_SL; ++j) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k <= 2 * SS_R; ++k) acc = fmaf(win.w[k], col[j + k], acc);
+            st[t][j] = acc;
+        }
+    }
     float ssum = 0.f, l1sum = 0.f;
 #pragma unroll
-    for (int j = 0; j < SS_ROWS; ++j) {
-        const int r = r0 + 8 * j;
+    for (int j = 0; j < SS_SL; ++j) {
+        const int r = rb + j;
         const int x = x0 + c, y = y0 + r;
         if (x >= b.W || y >= b.H) continue;
-        float mx = 0.f, my = 0.f, a = 0.f, bb = 0.f, cc = 0.f;
-#pragma unroll
-        for (int k = 0; k <= 2 * SS_R; ++k) {
-            const float w = win.w[k];
-            mx = fmaf(w, hs[0][r + k][c], mx);
-            my = fmaf(w, hs[1][r + k][c], my);
-            a = fmaf(w, hs[2][r + k][c], a);
-            bb = fmaf(w, hs[3][r + k][c], bb);
-            cc = fmaf(w, hs[4][r + k][c], cc);
-        }
+        const float mx = st[0][j], my = st[1][j], a = st[2][j], bb = st[3][j], cc = st[4][j];
         const float A1 = 2.f * mx * my + kC1;
         const float A2 = 2.f * (cc - mx * my) + kC2;
         const float B1 = mx * mx + my * my + kC1;
@@ -162,35 +191,48 @@ k_ssim_bwd(const float* __restrict__ img, const float* __restrict__ tgt, SViews 
     stage(da + b.plane, b.W, b.H, x0, y0, s1);
     stage(dc + b.plane, b.W, b.H, x0, y0, s2);
     __syncthreads();
-    for (int i = threadIdx.x; i < SS_E * SS_T; i += SS_THREADS) {
-        const int r = i / SS_T, c = i % SS_T;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    for (int it = threadIdx.x; it < SS_E * (SS_T / SS_SL); it += SS_THREADS) {
+        const int r = it / (SS_T / SS_SL), c0 = (it % (SS_T / SS_SL)) * SS_SL;
+        float v0[SS_SL + 2 * SS_R], v1[SS_SL + 2 * SS_R], v2[SS_SL + 2 * SS_R];
 #pragma unroll
-        for (int k = 0; k <= 2 * SS_R; ++k) {
-            const float w = win.w[k];
-            a0 = fmaf(w, s0[r][c + k], a0);
-            a1 = fmaf(w, s1[r][c + k], a1);
-            a2 = fmaf(w, s2[r][c + k], a2);
+        for (int q = 0; q < SS_SL + 2 * SS_R; ++q) { v0[q] = s0[r][c0 + q]; v1[q] = s1[r][c0 + q]; v2[q] = s2[r][c0 + q]; }
+#pragma unroll
+        for (int o = 0; o < SS_SL; ++o) {
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+            for (int k = 0; k <= 2 * SS_R; ++k) {
+                const float w = win.w[k];
+                a0 = fmaf(w, v0[o + k], a0);
+                a1 = fmaf(w, v1[o + k], a1);
+                a2 = fmaf(w, v2[o + k], a2);
+            }
+            hs[0][r][c0 + o] = a0; hs[1][r][c0 + o] = a1; hs[2][r][c0 + o] = a2;
         }
-        hs[0][r][c] = a0; hs[1][r][c] = a1; hs[2][r][c] = a2;
     }
     __syncthreads();
-    const int c = threadIdx.x & 31, r0 = threadIdx.x >> 5;
+    const int c = threadIdx.x & 31, rb = (threadIdx.x >> 5) * SS_SL;
     // d/dx of the mean over views of (1 - lam) mean|x - y| + lam (1 - mean S)
     const float scale = 1.f / ((float)sv.n * 3.f * (float)b.W * (float)b.H);
+    float fs[3][SS_SL];  // filtered partial-derivative maps at this thread's outputs
 #pragma unroll
-    for (int j = 0; j < SS_ROWS; ++j) {
-        const int r = r0 + 8 * j;
+    for (int t = 0; t < 3; ++t) {
+        float col[SS_SL + 2 * SS_R];
+#pragma unroll
+        for (int q = 0; q < SS_SL + 2 * SS_R; ++q) col[q] = hs[t][rb + q][c];
+#pragma unroll
+        for (int j = 0; j < SS_SL; ++j) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k <= 2 * SS_R; ++k) acc = fmaf(win.w[k], col[j + k], acc);
+            fs[t][j] = acc;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < SS_SL; ++j) {
+        const int r = rb + j;
         const int x = x0 + c, y = y0 + r;
         if (x >= b.W || y >= b.H) continue;
-        float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-#pragma unroll
-        for (int k = 0; k <= 2 * SS_R; ++k) {
-            const float w = win.w[k];
-            f0 = fmaf(w, hs[0][r + k][c], f0);
-            f1 = fmaf(w, hs[1][r + k][c], f1);
-            f2 = fmaf(w, hs[2][r + k][c], f2);
-        }
+        const float f0 = fs[0][j], f1 = fs[1][j], f2 = fs[2][j];
         const size_t o = (size_t)b.plane + (size_t)y * b.W + x;
         const float xv = img[o], yv = tgt[o];
         const float dS = f0 + 2.f * xv * f1 + yv * f2;
