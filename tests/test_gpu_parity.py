@@ -347,6 +347,46 @@ def test_split_low_resolution_long_lists():
         assert ok, (worst, nbad)
 
 
+@pytest.mark.parametrize("tile", [8, 16])
+def test_binning_many_tiles_with_depth_ties(tile):
+    """Depth order over 30 radix tiles plus a ragged tail, with most keys tied:
+    two exact planes (every Gaussian of a plane has the same depth bits, so
+    only stability across tiles puts them in index order), a few scattered
+    depths, some Gaussians behind the camera and some off-screen.  The lists
+    must equal the oracle's (tile, depth bits, index) order bit for bit."""
+    rng = np.random.default_rng(77)
+    W, H, f = 320, 200, 200.0
+    P = 30 * 2048 + 1001
+    z = np.where(rng.random(P) < 0.45, 3.0, 5.0)
+    scatter = rng.random(P) < 0.1
+    z[scatter] = rng.uniform(2.0, 8.0, size=int(scatter.sum()))
+    behind = rng.random(P) < 0.05
+    z[behind] = -1.0
+    u = rng.uniform(-10.0, W + 10.0, size=P)
+    v = rng.uniform(-10.0, H + 10.0, size=P)
+    off = rng.random(P) < 0.05
+    u[off] += 5000.0
+    g = np.zeros((P, synth.NPARAM))
+    g[:, 0] = (u - W / 2) * z / f
+    g[:, 1] = (v - H / 2) * z / f
+    g[:, 2] = z
+    g[:, 3:6] = rng.normal(-4.0, 0.3, size=(P, 3))
+    g[:, 6] = 1.0
+    g[:, 10] = 0.5
+    cam = U.identity_cam(W, H, f)
+    rz, params, gcam, fr, k, ocam, g64, _ = _setup(g, cam, tile=tile)
+    rec = _records(rz, P)
+    vis = rec["radius"] > 0
+    keys = rec["key"][vis]
+    assert vis.sum() > 40000 and (~vis).sum() > 1000
+    assert len(keys) - len(np.unique(keys)) > 30000  # most keys are ties
+    ob = oracle.bin_sort(rec["uv"], rec["radius"], rec["key"], W, H, tile)
+    gid, ranges = _gpu_bins(rz, fr)
+    assert fr.M == ob["M"] == int(rec["tiles"].sum())
+    np.testing.assert_array_equal(gid, ob["gid"])
+    np.testing.assert_array_equal(ranges, ob["ranges"])
+
+
 def test_empty_and_all_culled():
     cam = U.identity_cam(40, 24, 50.0)
     bg = (0.2, 0.5, 0.9)
