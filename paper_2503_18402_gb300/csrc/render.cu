@@ -119,6 +119,13 @@ __device__ inline float ex2_approx(float x)
     return y;
 }
 
+// Forward: list entries evaluated per loop iteration (a launch-shape constant;
+// the result does not depend on it).
+#ifndef DG_FWD_UNROLL
+#define DG_FWD_UNROLL 2
+#endif
+constexpr int kFwdUnroll = DG_FWD_UNROLL;
+
 constexpr float kLog2e = 1.4426950408889634f;
 // log2(1/255): the alpha >= 1/255 test is taken in the log2 domain, before the
 // exponential, identically in the forward and the backward
@@ -440,26 +447,30 @@ k_render_fwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                 T[k] = Tn;
             }
         };
-        // two entries per iteration: their quadratic forms do not depend on the
-        // transmittance chain, so both are evaluated before either is blended
-        for (int kk = 0; kk < cnt && !alldone; kk += 2) {
-            const int k1 = kk + 1 < cnt ? kk + 1 : kk;
-            const float4 a0 = s_a[kk], a1 = s_a[k1];
-            const float2 q0 = s_q[kk], q1 = s_q[k1];
-            const float dx0 = a0.x - pxc, dx1 = a1.x - pxc;
-            const float adx0 = a0.z * dx0, adx1 = a1.z * dx1;
-            float p0[PPT], p1[PPT];
+        // DG_FWD_UNROLL entries per iteration: their quadratic forms do not depend
+        // on the transmittance chain, so all are evaluated before any is blended
+        for (int kk = 0; kk < cnt && !alldone; kk += kFwdUnroll) {
+            float pu[kFwdUnroll][PPT], eu[kFwdUnroll][PPT];
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                const float dy0 = a0.y - pyc[k], dy1 = a1.y - pyc[k];
-                p0[k] = fmaf(dx0, fmaf(a0.w, dy0, adx0), q0.x * dy0 * dy0);
-                p1[k] = fmaf(dx1, fmaf(a1.w, dy1, adx1), q1.x * dy1 * dy1);
+            for (int u = 0; u < kFwdUnroll; ++u) {
+                const int ku = kk + u < cnt ? kk + u : cnt - 1;
+                const float4 a = s_a[ku];
+                const float2 q = s_q[ku];
+                const float dx = a.x - pxc;
+                const float adx = a.z * dx;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    const float dy = a.y - pyc[k];
+                    pu[u][k] = fmaf(dx, fmaf(a.w, dy, adx), q.x * dy * dy);
+                    eu[u][k] = pu[u][k] + q.y;
+                }
             }
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) blend(k, kk, p0[k], p0[k] + q0.y);
-            if (k1 != kk) {
+            for (int u = 0; u < kFwdUnroll; ++u) {
+                if (kk + u < cnt) {
 #pragma unroll
-                for (int k = 0; k < PPT; ++k) blend(k, k1, p1[k], p1[k] + q1.y);
+                    for (int k = 0; k < PPT; ++k) blend(k, kk + u, pu[u][k], eu[u][k]);
+                }
             }
             alldone = true;
 #pragma unroll

@@ -90,6 +90,9 @@ class Rasterizer:
         self.packed = (torch.empty(n * capi.PACKED_RECORD_BYTES, dtype=torch.uint8, device=d)
                        if self.opts.record == 1 else None)
         self.M_dev = torch.zeros(1, dtype=torch.int64, device=d)
+        # pinned landing slot of the pair count: one async copy and one event wait
+        self.M_host = torch.zeros(1, dtype=torch.int64).pin_memory()
+        self.M_event = torch.cuda.Event()
         self.status = torch.zeros(1, dtype=torch.int32, device=d)
         self.N_cap = N
         self.ws = None
@@ -184,8 +187,11 @@ class Rasterizer:
         self._ensure_ws(P, V, max(self.M_cap, 1))
         capi.dg_bin_count(self.depth, self.tiles, P, V, self.ws, self.ws.numel(), self.M_cap, self.M_dev, stream)
         self._mark("bin_count")
-        stream.synchronize()
-        M = int(self.M_dev.item())
+        with torch.cuda.stream(stream):
+            self.M_host.copy_(self.M_dev, non_blocking=True)
+        self.M_event.record(stream)
+        self.M_event.synchronize()
+        M = int(self.M_host[0])
         if M > self.M_cap:
             self._ensure_ws(P, V, int(M * self.headroom) + 1024)
             capi.dg_bin_count(self.depth, self.tiles, P, V, self.ws, self.ws.numel(), self.M_cap, self.M_dev, stream)
