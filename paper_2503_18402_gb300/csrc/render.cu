@@ -125,6 +125,11 @@ __device__ inline float ex2_approx(float x)
 #define DG_FWD_UNROLL 2
 #endif
 constexpr int kFwdUnroll = DG_FWD_UNROLL;
+// Backward: list entries whose quadratic forms are formed per loop iteration.
+#ifndef DG_BWD_UNROLL
+#define DG_BWD_UNROLL 1
+#endif
+constexpr int kBwdUnroll = DG_BWD_UNROLL;
 
 constexpr float kLog2e = 1.4426950408889634f;
 // log2(1/255): the alpha >= 1/255 test is taken in the log2 domain, before the
@@ -742,15 +747,12 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
             s_col[slot] = make_float4(gb.z, gb.w, gc, __int_as_float(j));
         }
         __syncthreads();
-        for (int kk = cnt - 1; kk >= 0; --kk) {
-            const float4 col = s_col[kk];
+        // one list entry, given its quadratic forms at this thread's pixels
+        auto entry = [&](int kk, const float4& col, float dx, const float* dyv, const float* pv) {
             const int pos = __float_as_int(col.w);
-            if (!__any_sync(0xffffffffu, pos < mylast)) continue;
-            const float4 a = s_a[kk];
-            const float2 q = s_q[kk];
+            if (!__any_sync(0xffffffffu, pos < mylast)) return;
             const float cr = col.x, cg = col.y, cb = col.z;
-            const float dx = a.x - pxc;
-            const float adx = a.z * dx;
+            const float qy = s_q[kk].y;
             if (PPT > 1) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) vd[i] = 0.f;
@@ -760,9 +762,9 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
             for (int k = 0; k < PPT; ++k) {
                 if (pos < lastp[k]) {
                     // the forward's blend test and alpha, bit for bit
-                    const float dy = a.y - pyc[k];
-                    const float p = fmaf(dx, fmaf(a.w, dy, adx), q.x * dy * dy);
-                    const float e = p + q.y;
+                    const float dy = dyv[k];
+                    const float p = pv[k];
+                    const float e = p + qy;
                     if (p <= 0.f && e >= kLog2AlphaMin) {
                         const float raw = ex2_approx(e);
                         const float alpha = fminf(kAlphaMax, raw);
@@ -779,9 +781,9 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                         // below the clamp: d alpha / d o = exp(power), d alpha / d power = alpha
                         const float dp = raw <= kAlphaMax ? dLda * alpha : 0.f;
                         const float dopa = raw <= kAlphaMax ? dLda * raw * kc.w : 0.f;
-                        const float qx = dp * dx, qy = dp * dy;
-                        const float v[9] = {-fmaf(kc.x, qx, kc.y * qy), -fmaf(kc.y, qx, kc.z * qy),
-                                            -0.5f * qx * dx, -qx * dy, -0.5f * qy * dy, dopa,
+                        const float qx = dp * dx, qdy = dp * dy;
+                        const float v[9] = {-fmaf(kc.x, qx, kc.y * qdy), -fmaf(kc.y, qx, kc.z * qdy),
+                                            -0.5f * qx * dx, -qx * dy, -0.5f * qdy * dy, dopa,
                                             wT * g0[k], wT * g1[k], wT * g2[k]};
 #pragma unroll
                         for (int i = 0; i < 9; ++i) vd[i] = PPT == 1 ? v[i] : vd[i] + v[i];
@@ -789,7 +791,7 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                 }
             }
             const unsigned anym = __ballot_sync(0xffffffffu, any);
-            if (!anym) continue;
+            if (!anym) return;
             if (kBwdDirectLanes > 0 && __popc(anym) <= kBwdDirectLanes) {
                 // few contributing lanes: each adds its own partial sums (three
                 // vector atomics) instead of the 12-shuffle warp reduction
@@ -799,7 +801,7 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                     atomicAdd(gp + 1, make_float4(vd[4], vd[5], vd[6], vd[7]));
                     atomicAdd((float*)(gp + 2), vd[8]);
                 }
-                continue;
+                return;
             }
             float vals[9];
 #pragma unroll
@@ -807,6 +809,29 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
             int idx;
             const float tot = warp_sum9(vals, lane, &idx);
             if (idx >= 0) atomicAdd((float*)(grad2d + 3 * (size_t)s_g[kk]) + idx, tot);
+        };
+        // kBwdUnroll entries per iteration, back to front: their quadratic forms
+        // are formed first (independent of the transmittance chain)
+        for (int kk = cnt - 1; kk >= 0; kk -= kBwdUnroll) {
+            float4 colu[kBwdUnroll];
+            float dxu[kBwdUnroll], dyu[kBwdUnroll][PPT], pu[kBwdUnroll][PPT];
+#pragma unroll
+            for (int u = 0; u < kBwdUnroll; ++u) {
+                const int ku = kk - u >= 0 ? kk - u : kk;
+                colu[u] = s_col[ku];
+                const float4 a = s_a[ku];
+                const float2 q = s_q[ku];
+                dxu[u] = a.x - pxc;
+                const float adx = a.z * dxu[u];
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    dyu[u][k] = a.y - pyc[k];
+                    pu[u][k] = fmaf(dxu[u], fmaf(a.w, dyu[u][k], adx), q.x * dyu[u][k] * dyu[u][k]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kBwdUnroll; ++u)
+                if (kk - u >= 0) entry(kk - u, colu[u], dxu[u], dyu[u], pu[u]);
         }
         __syncthreads();
     }
