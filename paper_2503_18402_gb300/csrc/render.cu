@@ -237,13 +237,19 @@ struct SplitCfg {
     int cap;   // chunk slots in the workspace
 };
 
-// Chunk length for M entries: requested or max(64, M/R), raised to 2M/cap so
-// that the chunks of split tiles (each tile has n > L, so ceil(n/L) < 2n/L)
-// never exceed the slots.
+// Shortest automatic chunk (entries): shorter chunks fill more CTAs but give
+// the combine pass more chunks to walk per pixel.
+#ifndef DG_SPLIT_MIN_LEN
+#define DG_SPLIT_MIN_LEN 64
+#endif
+
+// Chunk length for M entries: requested or max(DG_SPLIT_MIN_LEN, M/R), raised
+// to 2M/cap so that the chunks of split tiles (each tile has n > L, so
+// ceil(n/L) < 2n/L) never exceed the slots.
 __host__ __device__ inline int split_len(long long M, SplitCfg s)
 {
     long long L = s.Lreq > 0 ? s.Lreq : (M + s.R - 1) / s.R;
-    if (s.Lreq <= 0 && L < 64) L = 64;
+    if (s.Lreq <= 0 && L < DG_SPLIT_MIN_LEN) L = DG_SPLIT_MIN_LEN;
     const long long Lcap = (2 * M + s.cap - 1) / s.cap;
     if (L < Lcap) L = Lcap;
     if (L < 1) L = 1;
@@ -552,27 +558,56 @@ k_render_combine(const uint2* __restrict__ ranges, RViews rv, const RHdr* hdr, c
         const int n = (int)(rg.y - rg.x);
         const int nch = w.z;
         const size_t p = (size_t)threadIdx.x;
-        float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tf = -1.f;
-        int lastv = 0, nb = 0, ex = n;
-        for (int c = 0; c < nch; ++c) {
-            const size_t s = (size_t)(w.w + c) * NPIX + p;
-            const int lt = sl.last[s];
-            C0 += sl.c0[s]; C1 += sl.c1[s]; C2 += sl.c2[s];
-            lastv = max(lastv, lt & (kStopFlag - 1));
-            nb += sl.nbl[s];
-            if ((lt & kStopFlag) && Tf < 0.f) {
-                Tf = sl.tout[s];
-                ex = sl.stop[s] + 1;
+        // A few tiles hold dozens of chunks each and only their blocks work, so
+        // each walk loads CB chunks' fields before using any (chunk order, and
+        // so every sum's rounding, unchanged).
+        constexpr int CB = 8;
+        float C0 = 0.f, C1 = 0.f, C2 = 0.f;
+        int lastv = 0, nb = 0, cstop = -1;
+        for (int cb = 0; cb < nch; cb += CB) {
+            int lt[CB], nbv[CB];
+            float a0[CB], a1[CB], a2[CB];
+#pragma unroll
+            for (int j = 0; j < CB; ++j) {
+                if (cb + j < nch) {
+                    const size_t s = (size_t)(w.w + cb + j) * NPIX + p;
+                    lt[j] = sl.last[s]; nbv[j] = sl.nbl[s];
+                    a0[j] = sl.c0[s]; a1[j] = sl.c1[s]; a2[j] = sl.c2[s];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < CB; ++j) {
+                if (cb + j < nch) {
+                    C0 += a0[j]; C1 += a1[j]; C2 += a2[j];
+                    lastv = max(lastv, lt[j] & (kStopFlag - 1));
+                    nb += nbv[j];
+                    if ((lt[j] & kStopFlag) && cstop < 0) cstop = cb + j;
+                }
             }
         }
-        if (Tf < 0.f) Tf = sl.tout[(size_t)(w.w + nch - 1) * NPIX + p];
+        // T at the end: from the chunk where the pixel stopped, else the last chunk
+        const size_t sf = (size_t)(w.w + (cstop >= 0 ? cstop : nch - 1)) * NPIX + p;
+        const float Tf = sl.tout[sf];
+        const int ex = cstop >= 0 ? sl.stop[sf] + 1 : n;
         // colour behind each chunk (the backward's starting S), back to front
         float S0 = Tf * rv.bg0, S1 = Tf * rv.bg1, S2 = Tf * rv.bg2;
-        for (int c = nch - 1; c >= 0; --c) {
-            const size_t s = (size_t)(w.w + c) * NPIX + p;
-            const float a0 = sl.c0[s], a1 = sl.c1[s], a2 = sl.c2[s];
-            sl.c0[s] = S0; sl.c1[s] = S1; sl.c2[s] = S2;
-            S0 += a0; S1 += a1; S2 += a2;
+        for (int cb = nch - 1; cb >= 0; cb -= CB) {
+            float a0[CB], a1[CB], a2[CB];
+#pragma unroll
+            for (int j = 0; j < CB; ++j) {
+                if (cb - j >= 0) {
+                    const size_t s = (size_t)(w.w + cb - j) * NPIX + p;
+                    a0[j] = sl.c0[s]; a1[j] = sl.c1[s]; a2[j] = sl.c2[s];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < CB; ++j) {
+                if (cb - j >= 0) {
+                    const size_t s = (size_t)(w.w + cb - j) * NPIX + p;
+                    sl.c0[s] = S0; sl.c1[s] = S1; sl.c2[s] = S2;
+                    S0 += a0[j]; S1 += a1[j]; S2 += a2[j];
+                }
+            }
         }
         const size_t HW = (size_t)W * H;
         const size_t pix = (size_t)y * W + x;
