@@ -81,7 +81,7 @@ STAGE_SOURCE = {"render_fwd": "render.cu", "render_bwd": "render.cu", "project":
                 "project_bwd": "project.cu", "project_bwd_adam": "project.cu", "adam": "optim.cu"}
 
 
-def measured_traffic(stage: str):
+def measured_traffic(stage: str, root: str = ROOT):
     """DRAM bytes per launch of the stage's kernel from a committed ncu summary
     under profiles/ (lines 'stage:', 'source_sha1:', 'dram_bytes_per_launch:'),
     or None when there is none or it was taken on another version of the
@@ -91,9 +91,12 @@ def measured_traffic(stage: str):
     src = STAGE_SOURCE.get(stage)
     if src is None:
         return None
-    with open(os.path.join(ROOT, "paper_2503_18402_gb300", "csrc", src), "rb") as f:
-        sha = hashlib.sha1(f.read()).hexdigest()
-    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+    try:
+        with open(os.path.join(root, "paper_2503_18402_gb300", "csrc", src), "rb") as f:
+            sha = hashlib.sha1(f.read()).hexdigest()
+    except OSError:
+        return None
+    for path in sorted(glob.glob(os.path.join(root, "profiles", "*.md"))):
         kv = {}
         for line in open(path):
             if ":" in line and not line.startswith((" ", "|", "#")):
