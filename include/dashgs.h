@@ -82,8 +82,7 @@ typedef struct dg_camera {
  * diagonal, px^2 (0.3); bg: background colour composited with the final
  * transmittance; pixels_per_thread: pixels each render thread owns (1, 2 or
  * 4 with tile 16, 1 or 2 with tile 8; 0 = the library's default per pass);
- * split_len: list
- * splitting of the render passes: a tile whose sorted list is longer than L
+ * split_len: list splitting of the render passes: a tile whose sorted list is longer than L
  * entries is composited as ceil(n/L) chunks in parallel (Eq. 1 composes over
  * chunks through the transmittance product); 0 = automatic (split when the
  * batch has fewer tiles than twice the resident CTAs, L = max(64, M / resident

@@ -702,6 +702,68 @@ def test_batched_views_match_single_view_renders():
         np.testing.assert_array_equal(G.np_(rzb.blended[v]), orf["blended"])
 
 
+def test_max_views_per_call():
+    """DG_MAX_VIEWS (16) views in one call, the largest batch: each view's
+    render equals its single-view render bit for bit, the summed parameter
+    gradient equals the sum of the single-view gradients, the fused adjoint +
+    Adam equals the two calls; a 17th view is rejected before any launch."""
+    V = 16
+    g = synth.random_gaussians(4000, 41)
+    g[:, 3:6] += 0.3
+    g[-40:, 0] = 100.0  # culled in every view
+    sizes = [(40 + 8 * (i % 4), 30 + 5 * (i % 3)) for i in range(V)]
+    cams = [G.gpu_camera(synth.camera_cfg0(W, H, 3.5 + 0.15 * i)) for i, (W, H) in enumerate(sizes)]
+    # (lists never split: the automatic rule splits the small single-view
+    # batches and not the 16-view one, which changes the rounding order)
+    opts = capi.raster_opts(tile=8, bg=(0.1, 0.2, 0.3), split_len=-1)
+    P = g.shape[0]
+    params = G.gpu_params(g)
+    rzb = Rasterizer("cuda", opts)
+    frb = rzb.forward(params, P, cams)
+    rng = np.random.default_rng(16)
+    dLs = [(rng.normal(size=(3, H, W)) / (3 * 40 * 30)).astype(np.float32) for W, H in sizes]
+    dL = torch.from_numpy(np.concatenate([d.reshape(-1) for d in dLs])).cuda()
+    gb = torch.empty_like(params)
+    rzb.backward(params, frb, dL, gb)
+    torch.cuda.synchronize()
+    assert int(G.np_(rzb.status)[0]) == 0
+    gsum = np.zeros((59, P))
+    for v in range(V):
+        rz = Rasterizer("cuda", opts)
+        fr = rz.forward(params, P, cams[v])
+        gv = torch.empty_like(params)
+        rz.backward(params, fr, torch.from_numpy(dLs[v]).cuda(), gv)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(G.np_(frb.images[v]), G.np_(fr.img))
+        np.testing.assert_array_equal(G.np_(frb.Ts[v]), G.np_(fr.T))
+        np.testing.assert_array_equal(G.np_(frb.lasts[v]), G.np_(fr.last))
+        gsum += G.np_(gv)
+    ok, worst, nbad = G.grad_close(G.np_(gb).T, gsum.T)
+    assert ok, (worst, nbad)
+    # the fused multi-view adjoint + Adam against the two calls
+    lr = np.linspace(1e-4, 1e-2, 59).astype(np.float32)
+    m0 = torch.from_numpy(rng.normal(size=(59, P)).astype(np.float32) * 1e-3).cuda()
+    v0 = torch.from_numpy(np.abs(rng.normal(size=(59, P))).astype(np.float32) * 1e-6).cuda()
+    p2, m2, v2 = params.clone(), m0.clone(), v0.clone()
+    grads2 = torch.zeros_like(params)
+    capi.dg_project_bwd_adam(p2, P, P, cams, V, opts, rzb.radius, rzb.clamp, rzb.grad2d, grads2, m2, v2, lr, 0.9,
+                             0.999, 1e-15, 3)
+    p4, m4, v4 = params.clone(), m0.clone(), v0.clone()
+    capi.dg_adam_step(p4, grads2, m4, v4, P, P, lr, 0.9, 0.999, 1e-15, 3)
+    torch.cuda.synchronize()
+    ok, worst, nbad = G.grad_close(G.np_(grads2).T, G.np_(gb).T)
+    assert ok, (worst, nbad)
+    for a, b in ((p2, p4), (m2, m4), (v2, v4)):
+        np.testing.assert_array_equal(G.np_(a), G.np_(b))
+    # one view more than the limit
+    cams17 = cams + [cams[0]]
+    grads = torch.zeros_like(params)
+    with pytest.raises(capi.DashGSError) as e:
+        capi.dg_project_bwd(params, P, P, cams17, V + 1, opts, rzb.radius, rzb.clamp, rzb.grad2d, grads)
+    assert e.value.status == capi.DG_ERR_ARG
+    assert capi.dg_bin_workspace_size(P, V + 1, 1000) == 0
+
+
 def test_sparse_adam_parity():
     rng = np.random.default_rng(9)
     P, stride = 1003, 1010
