@@ -190,15 +190,20 @@ class Rasterizer:
         with torch.cuda.stream(stream):
             self.M_host.copy_(self.M_dev, non_blocking=True)
         self.M_event.record(stream)
+        # the pair sort is queued before the count reaches the host, so the GPU
+        # runs on while the host waits; when the pairs exceed the capacity it
+        # only records DG_ERR_CAPACITY (nothing written) and is redone below
+        capi.dg_bin_sort(self.feat, self.radius, P, carr, V, B, self.ws, self.ws.numel(), self.M_cap, self.gid,
+                         self.ranges, self.status, stream)
+        self._mark("bin_sort")
         self.M_event.synchronize()
         M = int(self.M_host[0])
         if M > self.M_cap:
             self._ensure_ws(P, V, int(M * self.headroom) + 1024)
             capi.dg_bin_count(self.depth, self.tiles, P, V, self.ws, self.ws.numel(), self.M_cap, self.M_dev, stream)
+            capi.dg_bin_sort(self.feat, self.radius, P, carr, V, B, self.ws, self.ws.numel(), self.M_cap, self.gid,
+                             self.ranges, self.status, stream)
         self._mark("host_sync")
-        capi.dg_bin_sort(self.feat, self.radius, P, carr, V, B, self.ws, self.ws.numel(), self.M_cap, self.gid,
-                         self.ranges, self.status, stream)
-        self._mark("bin_sort")
         img = torch.empty(3 * npix, dtype=torch.float32, device=self.device)
         T = torch.empty(npix, dtype=torch.float32, device=self.device)
         last = torch.empty(npix, dtype=torch.int32, device=self.device)
