@@ -69,7 +69,8 @@ __device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v)
 // tile publishes at about the same time, the walk back to an inclusive word
 // takes about sqrt(2 t / OS_WINDOW) round trips instead of sqrt(2 t).
 constexpr int OS_WINDOW = 16;
-__device__ inline uint64_t os_lookback(const uint64_t* look, long long t, int stride, int d, int* err)
+__device__ inline uint64_t os_lookback(const uint64_t* look, long long t, int stride, int d, int* err,
+                                       int max_polls = kLbPolls)
 {
     uint64_t sum = 0;
     long long j = t;  // the window covers tiles j - OS_WINDOW .. j - 1
@@ -93,7 +94,7 @@ __device__ inline uint64_t os_lookback(const uint64_t* look, long long t, int st
         }
         j -= used;
         if (used < OS_WINDOW) {
-            if (++polls > kLbPolls) {
+            if (++polls > max_polls) {
                 atomicExch(err, DG_ERR_TIMEOUT);
                 return sum;
             }

@@ -466,3 +466,31 @@ extern "C" dg_status dg_bin_sort(const float* feat, const int32_t* radius, int64
     dg_note_launch();
     return dg_check_launch("bin_sort");
 }
+
+// ------------------------------------------------------------ look-back probe
+namespace dg {
+__global__ void k_lookback_probe(const uint64_t* look, long long t, int stride, int d, int max_polls,
+                                 uint64_t* sum, int* err)
+{
+    *err = 0;
+    __threadfence();
+    *sum = os_lookback(look, t, stride, d, err, max_polls);
+}
+}  // namespace dg
+
+extern "C" dg_status dg_lookback_probe(const uint64_t* look, int64_t tile, int32_t stride, int32_t digit,
+                                       int32_t max_polls, uint64_t* sum, int32_t* err, dg_stream stream)
+{
+    if (!sum || !err || (tile > 0 && !look)) { dg_set_error("null buffer"); return DG_ERR_ARG; }
+    if (tile < 0 || stride < 1 || digit < 0 || digit >= stride) {
+        dg_set_error("bad look-back probe: tile=%lld stride=%d digit=%d", (long long)tile, stride, digit);
+        return DG_ERR_ARG;
+    }
+    if (max_polls < 0 || max_polls > dg::kLbPolls) {
+        dg_set_error("max_polls %d outside 0..%d", max_polls, dg::kLbPolls);
+        return DG_ERR_ARG;
+    }
+    dg::k_lookback_probe<<<1, 1, 0, (cudaStream_t)stream>>>(look, tile, stride, digit, max_polls, sum, err);
+    dg_note_launch();
+    return dg_check_launch("lookback_probe");
+}

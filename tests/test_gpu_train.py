@@ -11,6 +11,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
+from oracle import schedule as sch  # noqa: E402
 from paper_2503_18402_gb300 import synth  # noqa: E402
 from paper_2503_18402_gb300.train import Trainer, TrainConfig, make_dataset  # noqa: E402
 
@@ -43,4 +44,10 @@ def test_training_improves_and_respects_budget(data, scheduled):
     if scheduled:
         assert tr.sched.m >= 1 and tr.sched.r_m >= 1.0
         assert res["iters_per_factor"].get("1", 0) < cfg.iters  # some iterations below full resolution
-        assert abs(tr.sched.P_fin - 5 * init.shape[0]) >= 0  # state carried through Eq. 5
+        # Eq. 5 state: P_fin(0) = 5 P_init, then one update per densification
+        # step with P_add = that step's candidate count
+        P_fin = 5.0 * init.shape[0]
+        for h in tr.history:
+            P_fin = sch.pfin_update(P_fin, h["n_cand"], cfg.gamma, cfg.eta)
+        assert tr.sched.P_fin == pytest.approx(P_fin, rel=1e-12)
+        assert tr.sched.P_fin >= 5.0 * init.shape[0]
