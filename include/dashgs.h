@@ -185,6 +185,24 @@ DG_API dg_status dg_bin_sort(const float* feat, const int32_t* radius, int64_t P
                       int32_t n_views, int32_t tile, void* ws, size_t ws_bytes, int64_t M_cap, uint32_t* gid,
                       uint32_t* ranges, int32_t* status, dg_stream stream);
 
+/* Diagnostic: runs, in one device thread, the bounded look-back wait that the
+ * depth-order passes of dg_bin_count use between thread blocks (decoupled
+ * look-back, Merrill & Garland 2016; the paper's rasterizer needs the sort of
+ * Sec. 3, the wait is this library's), so that its give-up path can be tested
+ * without starving a real pass.
+ * In:  look [tile][stride] uint64 look-back words (device): top two bits 0 =
+ *      not published, 1 = the tile's own count, 2 = the inclusive prefix up
+ *      to that tile, low 62 bits the count; the wait sums column `digit` of
+ *      tiles tile-1, tile-2, ... down to the nearest inclusive word;
+ *      max_polls: re-reads of an unpublished word before giving up
+ *      (0..2^20; the passes use 2^20, about a second).
+ * Out: *sum (device uint64): the counts summed (partial after a give-up);
+ *      *err (device int32): 0, or DG_ERR_TIMEOUT when the wait gave up.
+ * Errors: DG_ERR_ARG for null pointers, tile < 0, stride < 1, digit outside
+ * 0..stride-1, max_polls outside its range. */
+DG_API dg_status dg_lookback_probe(const uint64_t* look, int64_t tile, int32_t stride, int32_t digit,
+                                   int32_t max_polls, uint64_t* sum, int32_t* err, dg_stream stream);
+
 /* Mixed-precision records for the render calls (opts->record = 1): each
  * float32 record of dg_project becomes 24 bytes, u and v float32 (pixel
  * positions need the full mantissa at 1600 px), conic A, B, C and opacity
@@ -293,16 +311,21 @@ DG_API dg_status dg_opacity_reset(float* params, float* m, float* v, int64_t str
                                   dg_stream stream);
 
 /* L1 loss for callers that cannot allocate device memory (the paper has no
- * counterpart).  Some callers cannot call cudaMalloc: code inside graph-node or
- * stream host callbacks, plugins whose host application owns every device
- * allocation, loops that forbid allocator calls after start-up.  Same result as
+ * counterpart).  Some callers cannot call cudaMalloc: plugins whose host
+ * application owns every device allocation, and real-time loops that forbid
+ * allocator calls after start-up.  Call it from an ordinary host thread (never
+ * from a host function or callback enqueued on a stream, where no CUDA call is
+ * allowed).  Same result as
  * dg_loss_l1, but the per-block partial sums live in a fixed 4 KiB device array
  * inside this library (DG_L1_NOALLOC_BLOCKS floats), so no workspace is passed
  * and nothing is allocated.  n <= DG_L1_NOALLOC_MAX_N (2^28 values: at most
  * 1024 values summed per thread), else DG_ERR_ARG.  The first call on a device
- * looks up the array's device address with that device current (make that
- * first call before any stream capture).  Every call shares the array: calls
- * that overlap on the GPU (unordered streams) race on it. */
+ * (and again after that device's context was destroyed and recreated) looks up
+ * the array's device address with that device current; make that first call
+ * before any stream capture: if `stream` is capturing and no address is known
+ * yet for the current context, the call returns DG_ERR_ARG and launches
+ * nothing.  Every call shares the array: calls queued on one stream run in
+ * order, calls that overlap on the GPU (unordered streams) race on it. */
 #define DG_L1_NOALLOC_BLOCKS 1024
 #define DG_L1_NOALLOC_MAX_N (1024LL * 256LL * 1024LL)
 DG_API dg_status dg_loss_l1_noalloc(const float* img, const float* target, int64_t n, float* dL_dimg,
@@ -484,6 +507,38 @@ DG_API dg_status dg_schedule_step(const dg_schedule* s, int64_t iter, dg_sched_o
 /* Densification step: Eq. 5 update of P_fin with P_add, then as
  * dg_schedule_step (host). */
 DG_API dg_status dg_schedule_densify(dg_schedule* s, int64_t iter, int64_t P_add, dg_sched_out* out);
+
+/* The plain (unscheduled) arm as a schedule (host call): full resolution at
+ * every iteration (m = 0, r = 1, k_full = 0), so dg_schedule_step returns the
+ * full size and the backbone's position learning rate decaying log-linearly
+ * from lr_pos_init at iteration 0 to lr_pos_final at S (3DGS backbone, kept
+ * by the paper, Sec. 5 "Implementation Details"). */
+DG_API dg_status dg_schedule_init_plain(int32_t H, int32_t W, const dg_sched_params* p, dg_schedule* out);
+
+/* Number of Gaussians a densification step may add (host call).
+ * s non-null (primitive schedule, Sec. 4.3): Eq. 5 with P_add = n_cand (the
+ * Gaussians meeting the backbone's densification threshold), then Eq. 4's
+ * target P_k at `iter`, written to *out; budget = floor(P_k) - n_keep.
+ * s null (3DGS backbone): budget = n_cand (out untouched).
+ * Then, with P_cap > 0, budget <= P_cap - n_keep; finally budget >= 0.
+ * n_keep: Gaussians left after pruning. */
+DG_API dg_status dg_densify_budget(dg_schedule* s, int64_t iter, int64_t n_keep, int64_t n_cand, int64_t P_cap,
+                                   int64_t* budget, dg_sched_out* out);
+
+/* Camera of a render at width x height of the full-resolution camera `full`
+ * (host call): fx, cx scaled by width / full->width, fy, cy by height /
+ * full->height (in double, rounded once to float); the pose is unchanged.
+ * This is how the schedule's reduced-resolution renders (floor(H/r),
+ * floor(W/r)) see the scene (Sec. 4.2). */
+DG_API dg_status dg_camera_scale(const dg_camera* full, int32_t width, int32_t height, dg_camera* out);
+
+/* Adam hyper-parameters for V views per step (host call; the paper trains one
+ * view per iteration and has no counterpart): the batch-size rules of
+ * Grendel-GS (Zhao et al. 2024, "On Scaling Up 3D Gaussian Splatting
+ * Training"): every learning rate times sqrt(V), beta1 <- beta1^V,
+ * beta2 <- beta2^V, so that one step over V views moves the parameters about
+ * as far as V single-view steps.  lr: host float[59], in place. */
+DG_API dg_status dg_batch_adam_scale(int32_t views_per_step, float* lr, float* beta1, float* beta2);
 
 #ifdef __cplusplus
 }

@@ -24,13 +24,14 @@ DG_OK, DG_ERR_ARG, DG_ERR_CAPACITY, DG_ERR_TIMEOUT, DG_ERR_CUDA = 0, -1, -2, -3,
 
 MAX_VIEWS = 16
 EXPORTS = ("dg_last_error", "dg_abi_version", "dg_kernel_launches", "dg_project", "dg_bin_workspace_size", "dg_bin_count",
-           "dg_bin_sort", "dg_render_workspace_size", "dg_render_fwd", "dg_render_bwd", "dg_pack_records", "dg_project_bwd", "dg_project_bwd_adam",
+           "dg_bin_sort", "dg_lookback_probe", "dg_render_workspace_size", "dg_render_fwd", "dg_render_bwd", "dg_pack_records", "dg_project_bwd", "dg_project_bwd_adam",
            "dg_project_bwd_adam_dev",
            "dg_loss_workspace_size", "dg_ssim_workspace_size", "dg_loss_l1_dssim",
            "dg_loss_l1", "dg_loss_l1_noalloc", "dg_adam_step", "dg_adam_hparams_fill", "dg_adam_step_dev",
            "dg_sparse_adam_step", "dg_visibility", "dg_spectrum_workspace_size",
            "dg_spectrum_accumulate", "dg_spectrum_finalize", "dg_downsample_area", "dg_schedule_init",
-           "dg_schedule_step", "dg_schedule_densify", "dg_densify_stats", "dg_densify_workspace_size",
+           "dg_schedule_step", "dg_schedule_densify", "dg_schedule_init_plain", "dg_densify_budget",
+           "dg_camera_scale", "dg_batch_adam_scale", "dg_densify_stats", "dg_densify_workspace_size",
            "dg_densify_mark", "dg_densify_apply", "dg_mse", "dg_opacity_reset")
 L1_NOALLOC_MAX_N = 1024 * 256 * 1024
 
@@ -129,6 +130,7 @@ _SIGS = {
     "dg_bin_workspace_size": ([_I64, _I32, _I64], _SZ),
     "dg_bin_count": ([_P, _P, _I64, _I32, _P, _SZ, _I64, _P, _P], _ST),
     "dg_bin_sort": ([_P, _P, _I64, _CAM, _I32, _I32, _P, _SZ, _I64, _P, _P, _P, _P], _ST),
+    "dg_lookback_probe": ([_P, _I64, _I32, _I32, _I32, _P, _P, _P], _ST),
     "dg_render_workspace_size": ([_CAM, _I32, _OPT, _I64], _SZ),
     "dg_pack_records": ([_P, _I64, _P, _P], _ST),
     "dg_render_fwd": ([_P, _P, _P, _CAM, _I32, _OPT, _P, _P, _P, _P, _P, _P, _SZ, _P], _ST),
@@ -161,6 +163,11 @@ _SIGS = {
     "dg_schedule_init": ([_P, _I32, _I32, ctypes.POINTER(SchedParams), ctypes.POINTER(Schedule)], _ST),
     "dg_schedule_step": ([ctypes.POINTER(Schedule), _I64, ctypes.POINTER(SchedOut)], _ST),
     "dg_schedule_densify": ([ctypes.POINTER(Schedule), _I64, _I64, ctypes.POINTER(SchedOut)], _ST),
+    "dg_schedule_init_plain": ([_I32, _I32, ctypes.POINTER(SchedParams), ctypes.POINTER(Schedule)], _ST),
+    "dg_densify_budget": ([ctypes.POINTER(Schedule), _I64, _I64, _I64, _I64, ctypes.POINTER(_I64),
+                           ctypes.POINTER(SchedOut)], _ST),
+    "dg_camera_scale": ([_CAM, _I32, _I32, _CAM], _ST),
+    "dg_batch_adam_scale": ([_I32, ctypes.POINTER(_F), ctypes.POINTER(_F), ctypes.POINTER(_F)], _ST),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -235,6 +242,13 @@ def dg_bin_workspace_size(P, n_views, M_cap) -> int:
 
 def dg_bin_count(depth, tiles, P, n_views, ws, ws_bytes, M_cap, M_out, stream=None):
     _check(_lib.dg_bin_count(_a(depth), _a(tiles), P, n_views, _a(ws), ws_bytes, M_cap, _a(M_out), _s(stream)))
+
+
+def dg_lookback_probe(look, tile, stride, digit, max_polls, sum_out, err_out, stream=None):
+    _check(_lib.dg_lookback_probe(_a(look), tile, stride, digit, max_polls, _a(sum_out), _a(err_out), _s(stream)))
+
+
+LB_AGG, LB_INC = 1 << 62, 2 << 62  # look-back word states (count in the low 62 bits)
 
 
 def dg_bin_sort(feat, radius, P, cams, n_views, tile, ws, ws_bytes, M_cap, gid, ranges, status, stream=None):
@@ -387,6 +401,35 @@ def dg_schedule_densify(sched: Schedule, it, P_add) -> SchedOut:
     out = SchedOut()
     _check(_lib.dg_schedule_densify(ctypes.byref(sched), int(it), int(P_add), ctypes.byref(out)))
     return out
+
+
+def dg_schedule_init_plain(H, W, params: SchedParams) -> Schedule:
+    out = Schedule()
+    _check(_lib.dg_schedule_init_plain(H, W, ctypes.byref(params), ctypes.byref(out)))
+    return out
+
+
+def dg_densify_budget(sched, it, n_keep, n_cand, P_cap):
+    """-> (budget, SchedOut or None); sched None = the backbone (every candidate)."""
+    b = _I64(0)
+    out = SchedOut()
+    _check(_lib.dg_densify_budget(ctypes.byref(sched) if sched is not None else None, int(it), int(n_keep),
+                                  int(n_cand), int(P_cap), ctypes.byref(b), ctypes.byref(out)))
+    return int(b.value), (out if sched is not None else None)
+
+
+def dg_camera_scale(full: Camera, width, height) -> Camera:
+    out = Camera()
+    _check(_lib.dg_camera_scale(ctypes.byref(full), int(width), int(height), ctypes.byref(out)))
+    return out
+
+
+def dg_batch_adam_scale(views_per_step, lr, beta1, beta2):
+    """-> (lr list of 59, beta1, beta2) for views_per_step views per Adam step."""
+    arr = (_F * NPARAM)(*[float(x) for x in lr])
+    b1, b2 = _F(beta1), _F(beta2)
+    _check(_lib.dg_batch_adam_scale(int(views_per_step), arr, ctypes.byref(b1), ctypes.byref(b2)))
+    return list(arr), b1.value, b2.value
 
 
 def dg_densify_stats(grad2d, radius, P, cams, n_views, grad_accum, denom, max_radius, stream=None):
