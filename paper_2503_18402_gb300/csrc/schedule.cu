@@ -391,3 +391,74 @@ extern "C" dg_status dg_schedule_densify(dg_schedule* s, int64_t iter, int64_t P
     if (upd > s->P_fin) s->P_fin = upd;
     return dg_schedule_step(s, iter, out);
 }
+
+extern "C" dg_status dg_schedule_init_plain(int32_t H, int32_t W, const dg_sched_params* p, dg_schedule* out)
+{
+    if (!p || !out) { dg_set_error("null argument"); return DG_ERR_ARG; }
+    if (H <= 0 || W <= 0 || p->S <= 0) { dg_set_error("bad schedule parameters"); return DG_ERR_ARG; }
+    dg_schedule s;
+    memset(&s, 0, sizeof s);
+    s.p = *p;
+    s.H = H;
+    s.W = W;
+    s.m = 0;
+    s.X0 = s.Xm = 1.0;
+    s.r_m = 1.0;
+    s.X[0] = 1.0;
+    s.r[0] = 1.0;
+    s.s[0] = (double)p->S;
+    s.k_full = 0;  // full resolution from the start: the position LR decays from iteration 0
+    s.P_fin = 5.0 * p->P_init;
+    *out = s;
+    return DG_OK;
+}
+
+extern "C" dg_status dg_densify_budget(dg_schedule* s, int64_t iter, int64_t n_keep, int64_t n_cand, int64_t P_cap,
+                                       int64_t* budget, dg_sched_out* out)
+{
+    if (!budget || n_keep < 0 || n_cand < 0 || P_cap < 0 || (s && !out)) {
+        dg_set_error("bad argument");
+        return DG_ERR_ARG;
+    }
+    int64_t b = n_cand;  // 3DGS backbone: every candidate
+    if (s) {
+        // Eq. 5 with P_add = the candidate count, then Eq. 4's target; the
+        // budget is what the target leaves after the kept Gaussians
+        const dg_status st = dg_schedule_densify(s, iter, n_cand, out);
+        if (st != DG_OK) return st;
+        b = (int64_t)floor(out->P_target) - n_keep;
+    }
+    if (P_cap > 0 && b > P_cap - n_keep) b = P_cap - n_keep;
+    *budget = b > 0 ? b : 0;
+    return DG_OK;
+}
+
+extern "C" dg_status dg_camera_scale(const dg_camera* full, int32_t width, int32_t height, dg_camera* out)
+{
+    if (!full || !out) { dg_set_error("null argument"); return DG_ERR_ARG; }
+    if (width <= 0 || height <= 0 || full->width <= 0 || full->height <= 0) {
+        dg_set_error("bad image size %dx%d (full %dx%d)", width, height, full->width, full->height);
+        return DG_ERR_ARG;
+    }
+    const double sx = (double)width / (double)full->width, sy = (double)height / (double)full->height;
+    dg_camera c = *full;
+    c.fx = (float)((double)full->fx * sx);
+    c.cx = (float)((double)full->cx * sx);
+    c.fy = (float)((double)full->fy * sy);
+    c.cy = (float)((double)full->cy * sy);
+    c.width = width;
+    c.height = height;
+    *out = c;
+    return DG_OK;
+}
+
+extern "C" dg_status dg_batch_adam_scale(int32_t views_per_step, float* lr, float* beta1, float* beta2)
+{
+    if (views_per_step < 1 || !lr || !beta1 || !beta2) { dg_set_error("bad argument"); return DG_ERR_ARG; }
+    const double V = (double)views_per_step;
+    const double f = sqrt(V);
+    for (int i = 0; i < DG_NPARAM; ++i) lr[i] = (float)((double)lr[i] * f);
+    *beta1 = (float)pow((double)*beta1, V);
+    *beta2 = (float)pow((double)*beta2, V);
+    return DG_OK;
+}

@@ -14,14 +14,18 @@ Tanks&Temples, which are not available here; these seeded scenes stand in for
 them with the shapes and parameter distributions of the workloads):
   * ``random_gaussians``: means U[-1,1]^3, log-scales N(-3, 0.5), random unit
     quaternions, opacity logit N(0, 1), SH coefficients N(0, 0.2^2).
-  * ``textured_scene``: 90% of the Gaussians on 20 random planes and spheres
-    whose SH DC colour follows a seeded texture with a 1/f amplitude spectrum
-    (0.5 to 40 cycles per unit of surface coordinate, as natural images have)
-    over the surface coordinates, 10% on a uniform background shell of radius
-    12; the other parameters are drawn as in ``random_gaussians`` except the
-    log-scale mean, -4.5 instead of -3 (about 2 px instead of 10 px at
-    1237x822 for the 2M-Gaussian scene), so that the rendered views keep
-    real high-frequency content instead of a 10-px blur.
+  * ``textured_scene``: a dead-leaves layout (the classic model of
+    natural-image statistics): 400 plane patches and spheres with half-sizes
+    from the scale-invariant density p(s) ~ s^-3 on [0.04, 0.9], placed in
+    [-1.8, 1.8]^3, each with its own base colour and a seeded texture with a
+    1/f amplitude spectrum (32 plane waves, 0.5 to 40 cycles per unit of
+    surface coordinate) setting the SH DC colour; 90% of the Gaussians spread
+    over the surfaces in proportion to area, 10% on a background shell of
+    radius 12.  Each Gaussian's scale is the local spacing sqrt(area / count)
+    with a log-normal spread (std 0.3), so surfaces are closed and resolved
+    down to the Gaussian spacing (about a pixel at 1237x822 for 2M
+    Gaussians); quaternions, opacity logits and higher SH are drawn as in
+    ``random_gaussians``.
 """
 from __future__ import annotations
 

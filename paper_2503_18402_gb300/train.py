@@ -13,6 +13,13 @@ Per iteration k (Sec. 4; supplementary "Learning Rate", "Densification"):
 The plain arm renders every iteration at full resolution with the position
 learning rate decaying from iteration 0.
 
+Iterations count rendered views.  With V views per step (one multi-view
+launch per pass, one Adam update per step), step j renders views jV .. jV+V-1
+at the schedule's resolution for iteration jV, and the backbone's windows
+(densification, opacity reset, learning-rate decay) stay in views seen; the
+Adam hyper-parameters follow the batch-size rules of Grendel-GS (learning
+rates x sqrt(V), betas^V, `dg_batch_adam_scale`).
+
 Python here only orders the library calls and owns the device buffers
 (PyTorch allocations); it computes nothing of the method.
 """
@@ -92,6 +99,8 @@ class TrainConfig:
     # read once): 0.65 ms against 0.70 ms for the two kernels at 2M Gaussians;
     # sparse Adam always runs as its own kernel
     fused_adam: bool = True
+    # V > 1: Adam learning rates x sqrt(V) and betas ^ V (Grendel-GS batch rules)
+    batch_adam_scaling: bool = True
     seed: int = 0
 
 
@@ -134,6 +143,15 @@ class Trainer:
         self.gt_cache = {}
         self.stream = torch.cuda.current_stream(self.dev)
         self.sched = None
+        self.V = max(1, cfg.views_per_step)
+        self.n_steps = (cfg.iters + self.V - 1) // self.V
+        self.beta1, self.beta2 = 0.9, 0.999
+        if self.V > 1 and cfg.batch_adam_scaling:
+            _, self.beta1, self.beta2 = capi.dg_batch_adam_scale(self.V, [0.0] * 59, 0.9, 0.999)
+        # the iteration plan (render size, position LR) of the plain arm; the
+        # scheduled arm replaces it with the resolution schedule in init_schedule
+        self.plan_sched = capi.dg_schedule_init_plain(self.H, self.W, self._sched_params())
+        self._full_cams = {}
         self.history = []
         self.init_schedule_s = 0.0
         self.densify_until = cfg.densify_until
@@ -146,27 +164,28 @@ class Trainer:
         self.graph_captures = 0
 
     # ---------------------------------------------------------------- schedule
+    def _sched_params(self):
+        cfg = self.cfg
+        return capi.sched_params(cfg.iters, a=cfg.a, gamma=cfg.gamma, eta=cfg.eta, P_init=float(self.P),
+                                 P_cap=float(cfg.P_cap), lr_pos_init=cfg.lr_pos_init * cfg.extent,
+                                 lr_pos_final=cfg.lr_pos_final * cfg.extent)
+
     def init_schedule(self):
         t0 = time.perf_counter()
         cfg = self.cfg
         _, sat = spectrum_table(self.imgs, self.dev)
-        p = capi.sched_params(cfg.iters, a=cfg.a, gamma=cfg.gamma, eta=cfg.eta, P_init=float(self.P),
-                              P_cap=float(cfg.P_cap), lr_pos_init=cfg.lr_pos_init * cfg.extent,
-                              lr_pos_final=cfg.lr_pos_final * cfg.extent)
-        self.sched = capi.dg_schedule_init(sat, self.H, self.W, p)
+        self.sched = capi.dg_schedule_init(sat, self.H, self.W, self._sched_params())
+        if cfg.reso_sched:
+            self.plan_sched = self.sched
         if cfg.densify_until_full and cfg.prim_sched:
             self.densify_until = max(cfg.densify_until, int(self.sched.k_full))
         torch.cuda.synchronize()
         self.init_schedule_s = time.perf_counter() - t0
 
-    def _plan(self, k):
-        cfg = self.cfg
-        if self.sched is not None and cfg.reso_sched:
-            o = capi.dg_schedule_step(self.sched, k)
-            return o.r_mod, o.height, o.width, o.lr_pos
-        t = min(1.0, k / cfg.iters)
-        lr = math.exp((1 - t) * math.log(cfg.lr_pos_init * cfg.extent) + t * math.log(cfg.lr_pos_final * cfg.extent))
-        return 1, self.H, self.W, lr
+    def _plan(self, it):
+        """(r_mod, h, w, position LR) at iteration `it` (views rendered so far)."""
+        o = capi.dg_schedule_step(self.plan_sched, it)
+        return o.r_mod, o.height, o.width, o.lr_pos
 
     def _target(self, j, r, h, w):
         if r == 1:
@@ -183,11 +202,12 @@ class Trainer:
         key = (j, h, w)
         c = self._cam_cache.get(key)
         if c is None:
-            v = self.views[j]
-            fx, fy, cx, cy = v["intr"]
-            sx, sy = w / self.W, h / self.H
-            c = make_camera(np.asarray(v["viewmat"], np.float32).reshape(-1), (fx * sx, fy * sy, cx * sx, cy * sy),
-                            w, h)
+            full = self._full_cams.get(j)
+            if full is None:
+                v = self.views[j]
+                full = make_camera(np.asarray(v["viewmat"], np.float32).reshape(-1), v["intr"], self.W, self.H)
+                self._full_cams[j] = full
+            c = capi.dg_camera_scale(full, w, h)
             self._cam_cache[key] = c
         return c
 
@@ -199,8 +219,11 @@ class Trainer:
     # ---------------------------------------------------------------- step
     def _lr(self, lr_pos):
         cfg = self.cfg
-        return [lr_pos] * 3 + [cfg.lr_scale] * 3 + [cfg.lr_rot] * 4 + [cfg.lr_opacity] + [cfg.lr_dc] * 3 + \
+        lr = [lr_pos] * 3 + [cfg.lr_scale] * 3 + [cfg.lr_rot] * 4 + [cfg.lr_opacity] + [cfg.lr_dc] * 3 + \
             [cfg.lr_rest] * 45
+        if self.V > 1 and cfg.batch_adam_scaling:
+            lr, _, _ = capi.dg_batch_adam_scale(self.V, lr, 0.9, 0.999)
+        return lr
 
     def _step_batched(self, k):
         """V views per step through the multi-view calls; with cuda_graph the
@@ -208,13 +231,15 @@ class Trainer:
         cfg = self.cfg
         b = self.buf[self.cur]
         P = self.P
-        V = cfg.views_per_step
-        r, h, w, lr_pos = self._plan(k)
+        V = self.V
+        it = k * V
+        r, h, w, lr_pos = self._plan(it)
         js = [self._next_view() for _ in range(V)]
         cams = [self._camera(j, h, w) for j in js]
         targets = [self._target(j, r, h, w) for j in js]
         lr = self._lr(lr_pos)
-        stats_on = k < self.densify_until
+        b1, b2 = self.beta1, self.beta2
+        stats_on = it < self.densify_until
         if not cfg.cuda_graph:
             shape, rz, key = self.tuner.pick(V * h * w, P)
             e0 = self.tuner.start(self.stream)
@@ -230,7 +255,7 @@ class Trainer:
                 capi.dg_densify_stats(rz.grad2d, rz.radius, P, cams, V, self.acc, self.den, self.maxr, self.stream)
             if cfg.fused_adam and not cfg.sparse_adam:
                 capi.dg_project_bwd_adam(b["p"], self.cap, P, cams, V, rz.opts, rz.radius, rz.clamp, rz.grad2d,
-                                         None, b["m"], b["v"], lr, 0.9, 0.999, 1e-15, k + 1, self.stream)
+                                         None, b["m"], b["v"], lr, b1, b2, 1e-15, k + 1, self.stream)
             else:
                 capi.dg_project_bwd(params, self.cap, P, cams, V, rz.opts, rz.radius, rz.clamp, rz.grad2d,
                                     self.grads[:, :P], self.stream)
@@ -243,7 +268,7 @@ class Trainer:
         if P != self.graph_P:
             self.graphs.clear()
             self.graph_P = P
-        hp = capi.dg_adam_hparams_fill(lr, 0.9, 0.999, 1e-15, k + 1)
+        hp = capi.dg_adam_hparams_fill(lr, b1, b2, 1e-15, k + 1)
         key = (P, h, w, V, stats_on, self.cur)
         g = self.graphs.get(key)
         if g is None:
@@ -284,11 +309,11 @@ class Trainer:
             if getattr(self, "vis", None) is None or self.vis.numel() < self.cap:
                 self.vis = torch.zeros(self.cap, dtype=torch.uint8, device=self.dev)
             capi.dg_visibility(radius, P, V, self.vis, self.stream)
-            capi.dg_sparse_adam_step(b["p"], self.grads, b["m"], b["v"], self.cap, P, lr, 0.9, 0.999, 1e-15, k + 1,
-                                     self.vis, self.stream)
+            capi.dg_sparse_adam_step(b["p"], self.grads, b["m"], b["v"], self.cap, P, lr, self.beta1, self.beta2,
+                                     1e-15, k + 1, self.vis, self.stream)
         else:
-            capi.dg_adam_step(b["p"], self.grads, b["m"], b["v"], self.cap, P, lr, 0.9, 0.999, 1e-15, k + 1,
-                              self.stream)
+            capi.dg_adam_step(b["p"], self.grads, b["m"], b["v"], self.cap, P, lr, self.beta1, self.beta2, 1e-15,
+                              k + 1, self.stream)
 
     def dL_b(self, n):
         if getattr(self, "_dLb", None) is None or self._dLb.numel() < n:
@@ -307,15 +332,19 @@ class Trainer:
         return self.sws_batch
 
     def step(self, k):
+        """Step k: views kV .. kV+V-1.  The backbone's events (densification,
+        opacity reset) fire when their iteration falls inside the step."""
         cfg = self.cfg
-        if cfg.views_per_step > 1 or cfg.cuda_graph:
+        if self.V > 1 or cfg.cuda_graph:
             r, M = self._step_batched(k)
         else:
             r, M = self._step_single(k)
-        kk = k + 1
-        if cfg.densify_from <= kk <= self.densify_until and kk % cfg.densify_every == 0:
+        it0, it1 = k * self.V, (k + 1) * self.V
+        kk = it1 // cfg.densify_every * cfg.densify_every
+        if kk > it0 and cfg.densify_from <= kk <= self.densify_until:
             self.densify(kk)
-        if kk % cfg.opacity_reset_every == 0 and kk <= cfg.densify_until:
+        kk = it1 // cfg.opacity_reset_every * cfg.opacity_reset_every
+        if kk > it0 and kk <= cfg.densify_until:
             b = self.buf[self.cur]
             capi.dg_opacity_reset(b["p"], b["m"], b["v"], self.cap, self.P, 0.01, self.stream)
         return r, M
@@ -342,8 +371,7 @@ class Trainer:
         self.tuner.stop(key, shape, e0, self.stream)
         if k < self.densify_until:
             capi.dg_densify_stats(rz.grad2d, rz.radius, P, cam, 1, self.acc, self.den, self.maxr, self.stream)
-        lr = [lr_pos] * 3 + [cfg.lr_scale] * 3 + [cfg.lr_rot] * 4 + [cfg.lr_opacity] + [cfg.lr_dc] * 3 + \
-             [cfg.lr_rest] * 45
+        lr = self._lr(lr_pos)
         if cfg.fused_adam and not cfg.sparse_adam:
             rz.project_bwd_adam(b["p"], self.cap, fr, b["m"], b["v"], lr, k + 1, stream=self.stream)
         else:
@@ -369,12 +397,9 @@ class Trainer:
         capi.dg_densify_mark(b["p"], self.cap, P, self.acc, self.den, self.maxr, opts, self.dws, self.dws.numel(),
                              self.counts, self.stream)
         n_keep, n_cand = (int(x) for x in self.counts.cpu())
-        if self.sched is not None and cfg.prim_sched:
-            o = capi.dg_schedule_densify(self.sched, k, n_cand)
-            budget = max(0, int(o.P_target) - n_keep)
-        else:
-            budget = n_cand
-        budget = max(0, min(budget, cfg.P_cap - n_keep))
+        # Eq. 5 / Eq. 4 budget (primitive schedule) or every candidate (backbone), capped
+        sched = self.sched if (self.sched is not None and cfg.prim_sched) else None
+        budget, _ = capi.dg_densify_budget(sched, k, n_keep, n_cand, cfg.P_cap)
         n_sel = min(budget, n_cand)
         noise = torch.randn((max(n_sel, 1), 2, 3), generator=self.gen, device=self.dev)
         capi.dg_densify_apply(b["p"], b["m"], b["v"], self.cap, P, n_cand, budget, noise, self.dws, self.dws.numel(),
@@ -403,18 +428,18 @@ class Trainer:
         if cfg.scheduled:
             self.init_schedule()
         res_hist = {}
-        for k in range(cfg.iters):
+        for k in range(self.n_steps):
             r, M = self.step(k)
-            res_hist[r] = res_hist.get(r, 0) + 1
-            if log_every and (k + 1) % log_every == 0:
+            res_hist[r] = res_hist.get(r, 0) + self.V
+            if log_every and ((k + 1) * self.V) % log_every < self.V:
                 torch.cuda.synchronize()
-                print(json.dumps(dict(iter=k + 1, P=self.P, r=r, loss=float(self.loss[0].item()),
+                print(json.dumps(dict(iter=(k + 1) * self.V, P=self.P, r=r, loss=float(self.loss[0].item()),
                                       s=round(time.perf_counter() - t0, 2))), flush=True)
         torch.cuda.synchronize()
         self._check_pending(keep=0)
         return dict(seconds=time.perf_counter() - t0, schedule_init_s=self.init_schedule_s, P_final=self.P,
                     iters_per_factor={str(k): v for k, v in sorted(res_hist.items())},
-                    render_shapes=self.tuner.summary(), views_per_step=cfg.views_per_step,
+                    render_shapes=self.tuner.summary(), views_per_step=self.V, steps=self.n_steps,
                     cuda_graph=cfg.cuda_graph, graph_captures=self.graph_captures,
                     skipped_steps=self.skipped_steps)
 
@@ -443,7 +468,7 @@ def main(argv=None):
                          "only the primitive schedule; all = the four")
     ap.add_argument("--a", type=float, default=4.0, help="r_m from X(r_m) = X(1)/a (Sec. 4.2)")
     ap.add_argument("--gamma", type=float, default=0.98, help="Eq. 5 momentum")
-    ap.add_argument("--iters", type=int, default=30000)
+    ap.add_argument("--iters", type=int, default=30000, help="views rendered (steps x views per step)")
     ap.add_argument("--n-gt", type=int, default=2_000_000)
     ap.add_argument("--n-init", type=int, default=100_000)
     ap.add_argument("--views", type=int, default=160)
@@ -459,38 +484,66 @@ def main(argv=None):
     ap.add_argument("--mip2d", type=float, default=0.0, help="Mip-Splatting 2D filter variance (0: dilation)")
     ap.add_argument("--record", choices=["fp32", "mixed"], default="fp32",
                     help="render-side record storage (mixed: float16 conic/opacity, bfloat16 colour)")
+    ap.add_argument("--runs", nargs="*", default=None,
+                    help="several runs on one dataset, each 'arm[:key=value...]' with keys a, gamma, v (views per "
+                         "step), graph (0/1), record (fp32/mixed), sparse (0/1), mip2d, iters; e.g. plain "
+                         "scheduled:a=4:v=16:graph=1:record=mixed (default: the runs --arm names)")
     args = ap.parse_args(argv)
     from . import synth
     dev = torch.device("cuda")
     gt, cams, imgs, train, test = make_dataset(args.n_gt, args.views, args.width, args.height, dev)
     init = synth.perturb(gt, 3001, n_keep=args.n_init)
-    arms = {"both": ["plain", "scheduled"], "all": ["plain", "scheduled", "reso", "prim"]}.get(args.arm, [args.arm])
+    runs = args.runs or {"both": ["plain", "scheduled"],
+                         "all": ["plain", "scheduled", "reso", "prim"]}.get(args.arm, [args.arm])
     results = {}
-    for arm in arms:
-        cfg = TrainConfig(iters=args.iters, scheduled=(arm != "plain"), P_cap=args.p_cap,
-                          reso_sched=arm in ("scheduled", "reso"), prim_sched=arm in ("scheduled", "prim"),
-                          a=args.a, gamma=args.gamma, ssim_lambda=args.ssim_lambda, autotune=not args.no_autotune,
-                          views_per_step=args.views_per_step, cuda_graph=args.cuda_graph,
-                          record=1 if args.record == "mixed" else 0, sparse_adam=args.sparse_adam,
-                          mip2d=args.mip2d)
-        if args.iters < 30000:  # compress the backbone's iteration windows proportionally
-            s = args.iters / 30000
-            cfg.densify_from = max(1, int(500 * s)); cfg.densify_until = int(15000 * s)
-            cfg.densify_every = max(1, int(100 * s)); cfg.opacity_reset_every = max(1, int(3000 * s))
-        tr = Trainer(cfg, init, [cams[i] for i in train], [imgs[i] for i in train], dev)
-        res = tr.run(log_every=args.log_every)
-        res["psnr_test"] = tr.psnr([cams[i] for i in test], [imgs[i] for i in test])
-        res["densify_last"] = tr.history[-1] if tr.history else None
-        if tr.sched is not None:
-            s = tr.sched
-            res["schedule"] = dict(r_m=s.r_m, m=s.m, k_full=s.k_full, P_fin=s.P_fin,
-                                   anchors=[(s.s[i], s.r[i]) for i in range(s.m + 1)])
-        results[arm] = res
-        print(json.dumps({arm: res}), flush=True)
-        del tr
-        torch.cuda.empty_cache()
+    for spec in runs:
+        res, _ = train_run(spec, args, init, cams, imgs, train, test, dev)
+        results[spec] = res
+        print(json.dumps({spec: res}), flush=True)
     print(json.dumps(dict(config=vars(args), results=results)), flush=True)
     return results
+
+
+def parse_run(spec: str, args) -> TrainConfig:
+    """TrainConfig of one run spec 'arm[:key=value...]' (defaults from args)."""
+    parts = spec.split(":")
+    arm = parts[0]
+    if arm not in ("plain", "scheduled", "reso", "prim"):
+        raise ValueError(f"unknown arm {arm!r} in {spec!r}")
+    kv = dict(p.split("=", 1) for p in parts[1:])
+    iters = int(kv.pop("iters", args.iters))
+    cfg = TrainConfig(iters=iters, scheduled=(arm != "plain"), P_cap=args.p_cap,
+                      reso_sched=arm in ("scheduled", "reso"), prim_sched=arm in ("scheduled", "prim"),
+                      a=float(kv.pop("a", args.a)), gamma=float(kv.pop("gamma", args.gamma)),
+                      ssim_lambda=args.ssim_lambda, autotune=not args.no_autotune,
+                      views_per_step=int(kv.pop("v", args.views_per_step)),
+                      cuda_graph=bool(int(kv.pop("graph", int(args.cuda_graph)))),
+                      record=1 if kv.pop("record", args.record) == "mixed" else 0,
+                      sparse_adam=bool(int(kv.pop("sparse", int(args.sparse_adam)))),
+                      mip2d=float(kv.pop("mip2d", args.mip2d)))
+    if kv:
+        raise ValueError(f"unknown keys {sorted(kv)} in {spec!r}")
+    if iters < 30000:  # compress the backbone's iteration windows proportionally
+        s = iters / 30000
+        cfg.densify_from = max(1, int(500 * s)); cfg.densify_until = int(15000 * s)
+        cfg.densify_every = max(1, int(100 * s)); cfg.opacity_reset_every = max(1, int(3000 * s))
+    return cfg
+
+
+def train_run(spec, args, init, cams, imgs, train, test, dev):
+    """One training run; returns (result dict, its TrainConfig)."""
+    cfg = parse_run(spec, args)
+    tr = Trainer(cfg, init, [cams[i] for i in train], [imgs[i] for i in train], dev)
+    res = tr.run(log_every=args.log_every)
+    res["psnr_test"] = tr.psnr([cams[i] for i in test], [imgs[i] for i in test])
+    res["densify_last"] = tr.history[-1] if tr.history else None
+    if tr.sched is not None:
+        s = tr.sched
+        res["schedule"] = dict(r_m=s.r_m, m=s.m, k_full=s.k_full, P_fin=s.P_fin,
+                               anchors=[(s.s[i], s.r[i]) for i in range(s.m + 1)])
+    del tr
+    torch.cuda.empty_cache()
+    return res, cfg
 
 
 if __name__ == "__main__":
