@@ -36,6 +36,10 @@ N_GAUSS = 2_000_000
 N_VIEWS = 16
 BENCH_TILE = 8  # tile edge of the workload (the autotuner picks the rest of the launch shape)
 METRIC = "fwd+bwd rasterize ms/view (full-res training step incl. L1 + D-SSIM + Adam)"
+# training leg: the plain FP32 full-resolution arm (one view per iteration) and
+# the scheduled arms: 16 views per step in one launch per pass, each step one
+# CUDA-graph replay, mixed-precision records; a = 2 and the paper's a = 4
+TRAIN_RUNS = ("plain", "scheduled:a=2:v=16:graph=1:record=mixed", "scheduled:a=4:v=16:graph=1:record=mixed")
 # Algorithmic FP32 work of the compositing passes (Eq. 1 and its adjoint), per
 # (pixel, list entry): every entry a pixel examines needs its alpha test --
 # offsets, quadratic form, exponential, clamp, threshold; a blended entry adds
@@ -63,6 +67,10 @@ def parse():
                          "default: autotuned over the candidates")
     ap.add_argument("--separate-adam", action="store_true",
                     help="projection adjoint and Adam as two kernels (default: one fused kernel)")
+    ap.add_argument("--no-train", action="store_true",
+                    help="skip the 30k-iteration training leg (plain FP32 arm vs scheduled batched mixed arm)")
+    ap.add_argument("--train-runs", nargs="*", default=list(TRAIN_RUNS),
+                    help="training runs of the training leg (train.py run specs; the first is the baseline)")
     ap.add_argument("--no-c4-crop", action="store_true",
                     help="skip the CPU baseline's 6M-Gaussian crop measurement (scene generation takes ~30 s)")
     return ap.parse_args()
@@ -468,6 +476,8 @@ def run_ours(args):
     if graph_ms is not None:
         out["graph_ms_per_view"] = round(graph_ms, 4)
     out["clocks"] = clk
+    if not args.no_train:
+        out["training"] = training_leg(gt, dev, args, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(model, views[0], targets[0].double().cpu().numpy(), BENCH_TILE,
                                            c4_scene=not args.no_c4_crop)
@@ -475,6 +485,46 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- training
+def training_leg(gt, dev, args, gpu_index):
+    """The metric's first half: seconds to 30k iterations and held-out PSNR of
+    the plain FP32 full-resolution arm and of the scheduled arms, on this
+    scene (160 ring views at 1237x822 rendered from the ground truth, every
+    8th held out, 100k perturbed points to start).  Wall-clock of each run
+    includes the schedule's spectrum pass, excludes scene generation."""
+    import types
+
+    import torch
+
+    from paper_2503_18402_gb300 import synth, train
+    targs = types.SimpleNamespace(iters=30000, p_cap=3_000_000, a=4.0, gamma=0.98, ssim_lambda=0.2,
+                                  no_autotune=False, views_per_step=1, cuda_graph=False, record="fp32",
+                                  sparse_adam=False, mip2d=0.0, log_every=0)
+    _, cams, imgs, tr_idx, te_idx = train.make_dataset(gt.shape[0], 160, W_FULL, H_FULL, dev, gt=gt)
+    init = synth.perturb(gt, 3001, n_keep=100_000)
+    runs = {}
+    clocks = Clocks(gpu_index)
+    clocks.start()
+    for spec in args.train_runs:
+        res, _ = train.train_run(spec, targs, init, cams, imgs, tr_idx, te_idx, dev)
+        runs[spec] = {"s": round(res["seconds"], 2), "psnr_db": round(res["psnr_test"], 3),
+                      "P_final": res["P_final"], "steps": res["steps"],
+                      "r_m": round(res["schedule"]["r_m"], 2) if "schedule" in res else None,
+                      "skipped_steps": res["skipped_steps"]}
+    clk = clocks.stop()
+    del imgs
+    torch.cuda.empty_cache()
+    base = runs[args.train_runs[0]]
+    for spec, r in runs.items():
+        if spec != args.train_runs[0]:
+            r["psnr_gap_db"] = round(r["psnr_db"] - base["psnr_db"], 3)
+            r["time_ratio"] = round(r["s"] / base["s"], 3)
+            r["matched"] = bool(r["psnr_db"] >= base["psnr_db"] - 0.1 and r["s"] < base["s"])
+    return {"metric": "s to 30k iterations at matched PSNR (held-out, within 0.1 dB of the first run)",
+            "scene": "textured 2M-Gaussian ground truth, 140 train / 20 held-out views at 1237x822, init 100k",
+            "baseline": args.train_runs[0], "runs": runs, "clocks": clk}
 
 
 # --------------------------------------------------------------------------- oracle (CPU)

@@ -873,6 +873,220 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
     }  // work items
 }
 
+// Backward of 8x8 tiles with one pixel per thread (64 threads, two warps of
+// 8x4 pixels), with entry-parallel gradient sums.  A staged batch of up to 64
+// entries is taken in groups of kEpG = 16, back to front; per group, each warp:
+//   A. pixel-parallel (lane = pixel): walks the group's entries back to front
+//      exactly as k_render_bwd (the forward's blend test bit for bit, T
+//      recovered through 1/(1 - alpha), dL/dalpha from the running g . S) and
+//      stores per (entry, pixel) the two scalars the gradient needs,
+//      dp = dL/dpower and wT = alpha T (0, 0 where the pixel does not blend).
+//      Four entries at a time: their tests, alphas and reciprocals do not
+//      depend on the transmittance chain and are formed first;
+//   B. entry-parallel (lane = entry of the group, one of two halves of the
+//      warp's 32 pixels): sums over its 16 pixels the nine partial gradients
+//      formed from (dp, wT), the entry's conic, the pixel's offset and its
+//      dL/dC; the two halves are added with one shuffle each and the entry's
+//      sums go out with three vector atomics when some pixel of the warp
+//      blended it.
+// Phase B runs on full warps: the gradient arithmetic per blended (pixel,
+// entry) of k_render_bwd (about 40 instructions on the lanes that blend, then
+// a 12-shuffle reduction or up to 16 lanes of atomics) becomes about 17
+// instructions per (pixel, entry) slot on all lanes.  Both phases touch only
+// the warp's own pixels, so only the staging needs the CTA barrier.  The
+// opacity term uses d alpha / d o = alpha / o below the clamp: sum(dp) / o.
+constexpr int kEpG = 16;
+constexpr int kEpPitch = 33;  // float2 per entry row of the (entry, pixel) matrix: 32 pixels + 1
+
+template <int REC>
+__global__ void __launch_bounds__(64, 16)
+k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
+                const uint2* __restrict__ ranges, RViews rv, RHdr* hdr, const int4* __restrict__ items, Slots sl,
+                const uint8_t* __restrict__ flags, long long flags_cap,
+                const float* __restrict__ Tfin, const int* __restrict__ lastin,
+                const float* __restrict__ dLdimg, float4* __restrict__ grad2d)
+{
+    constexpr int B = 8, NT = 64, NPIX = 64;
+    __shared__ float4 s_a[NT];    // u, v, a', b'  (the forward's prescaled conic)
+    __shared__ float2 s_q[NT];    // c', log2 o
+    __shared__ float4 s_k[NT];    // A, B, C, 1/o
+    __shared__ float4 s_col[NT];  // r, g, b, list position (int bits)
+    __shared__ uint32_t s_g[NT];
+    __shared__ float2 s_m[2][kEpG * kEpPitch];  // per warp: [entry][pixel] (dp, wT)
+    __shared__ float4 s_gp[2][32];               // per warp: dL/dC of its pixels
+    __shared__ int s_w[NT / 32];
+    __shared__ int s_n;
+    __shared__ int4 s_item;
+    const float bg0 = rv.bg0, bg1 = rv.bg1, bg2 = rv.bg2;
+    const bool planned = hdr->planned != 0 && items != nullptr;
+    const int L = planned ? hdr->L : INT_MAX;
+    const int count = planned ? hdr->n_items : rv.total;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    float2* sm = s_m[wp];
+    for (;;) {
+    const Item it = next_item(&hdr->cnt_bwd, count, planned ? items : nullptr, rv, &s_item);
+    if (it.tile < 0) break;
+    const int tile = it.tile, tx = it.tx, ty = it.ty, W = it.W, H = it.H;
+    int lx, ly0;
+    pix_of<B, 1>(threadIdx.x, &lx, &ly0);
+    const int x = tx * B + lx;
+    const int y = ty * B + ly0;
+    const float pxc = (float)x + 0.5f, pyc = (float)y + 0.5f;
+    const float tpx0 = (float)(tx * B) + 0.5f, tpx1 = tpx0 + (float)(B - 1);
+    const float tpy0 = (float)(ty * B) + 0.5f, tpy1 = tpy0 + (float)(B - 1);
+    const uint2 rg = ranges[tile];
+    const int nlist = (int)(rg.y - rg.x);
+    const bool split = it.slot0 >= 0;
+    const int lo = split ? it.c * L : 0;
+    const int hi = split ? (int)min((long long)nlist, (long long)lo + L) : nlist;
+    const size_t HW = (size_t)W * H;
+    float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, gS = 0.f;
+    int lastp = 0;
+    if (x < W && y < H) {
+        const size_t pix = (size_t)y * W + x;
+        const float* dl = dLdimg + 3 * it.poff;
+        lastp = lastin[it.poff + pix];
+        g0 = dl[pix];
+        g1 = dl[HW + pix];
+        g2 = dl[2 * HW + pix];
+        if (split) {
+            const size_t s = (size_t)(it.slot0 + it.c) * NPIX + (size_t)(ly0 * B + lx);
+            T = sl.tout[s];
+            gS = g0 * sl.c0[s] + g1 * sl.c1[s] + g2 * sl.c2[s];
+        } else {
+            T = Tfin[it.poff + pix];
+            gS = T * (g0 * bg0 + g1 * bg1 + g2 * bg2);
+        }
+    }
+    s_gp[wp][lane] = make_float4(g0, g1, g2, 0.f);
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    if (lastp > 0) atomicMax(&s_n, lastp);
+    __syncthreads();
+    const int top = min(s_n, hi);
+    // phase B: this lane's entry of the group and half of the warp's pixels
+    // (pixels 16 h .. 16 h + 15 = rows 2h, 2h + 1 of the warp's 8x4 block)
+    const int be = lane & (kEpG - 1), bh = lane >> 4;
+    const float bpx0 = tpx0, bpy0 = tpy0 + (float)(4 * wp + 2 * bh);
+    for (int base = top > lo ? lo + ((top - lo - 1) / NT) * NT : lo - 1; base >= lo; base -= NT) {
+        const int j = base + (int)threadIdx.x;
+        bool keep = false;
+        float4 ga, gb;
+        float gc = 0.f;
+        uint32_t g = 0;
+        if (j < top) {
+            const long long gj = (long long)rg.x + j;
+            if (flags && gj < flags_cap) {
+                keep = flags[gj] != 0;
+                if (keep) {
+                    g = gid[gj];
+                    load_record<REC>(feat, g, ga, gb, gc);
+                }
+            } else {
+                g = gid[gj];
+                load_record<REC>(feat, g, ga, gb, gc);
+                keep = !tile_skip(ga, gb, tpx0, tpx1, tpy0, tpy1);
+            }
+        }
+        int cnt;
+        const int slot = compact_index<NT>(keep, s_w, &cnt);
+        if (keep) {
+            s_g[slot] = g;
+            s_a[slot] = make_float4(ga.x, ga.y, -0.5f * kLog2e * ga.z, -kLog2e * ga.w);
+            s_q[slot] = make_float2(-0.5f * kLog2e * gb.x, __log2f(gb.y));
+            s_k[slot] = make_float4(ga.z, ga.w, gb.x, __frcp_rn(gb.y));
+            s_col[slot] = make_float4(gb.z, gb.w, gc, __int_as_float(j));
+        }
+        __syncthreads();
+        for (int kb = ((cnt - 1) / kEpG) * kEpG; kb >= 0 && cnt > 0; kb -= kEpG) {
+            const int ke = min(cnt, kb + kEpG);
+            // A: this lane's pixel over the group's entries, back to front, four at a time
+            uint32_t mine = 0;  // entries of the group this pixel blends (bit kk - kb)
+            for (int k0 = ke - 1; k0 >= kb; k0 -= 4) {
+                float al[4], iv[4], gcl[4];
+                bool bl[4], un[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int kk = k0 - u >= kb ? k0 - u : kb;
+                    const float4 col = s_col[kk];
+                    const float4 a = s_a[kk];
+                    const float2 q = s_q[kk];
+                    const float dx = a.x - pxc, dy = a.y - pyc;
+                    const float p = fmaf(dx, fmaf(a.w, dy, a.z * dx), q.x * dy * dy);
+                    const float e = p + q.y;
+                    bl[u] = k0 - u >= kb && __float_as_int(col.w) < lastp && p <= 0.f && e >= kLog2AlphaMin;
+                    const float raw = ex2_approx(e);
+                    al[u] = fminf(kAlphaMax, raw);
+                    un[u] = raw <= kAlphaMax;
+                    iv[u] = __fdividef(1.f, 1.f - al[u]);
+                    gcl[u] = fmaf(g0, col.x, fmaf(g1, col.y, g2 * col.z));
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (k0 - u < kb) break;
+                    float dpv = 0.f, wTv = 0.f;
+                    if (bl[u]) {
+                        T *= iv[u];
+                        wTv = al[u] * T;
+                        const float dLda = fmaf(T, gcl[u], -gS * iv[u]);
+                        gS = fmaf(wTv, gcl[u], gS);
+                        dpv = un[u] ? dLda * al[u] : 0.f;
+                        mine |= 1u << (k0 - u - kb);
+                    }
+                    sm[(k0 - u - kb) * kEpPitch + lane] = make_float2(dpv, wTv);
+                }
+            }
+            const uint32_t used = __reduce_or_sync(0xffffffffu, mine);
+            __syncwarp();
+            // B: entry kb + be over pixels 16 bh .. 16 bh + 15 of the warp
+            if (used) {
+                const int ek = kb + be;
+                const bool act = ek < ke && ((used >> be) & 1u);
+                float4 kc = make_float4(0.f, 0.f, 0.f, 0.f);
+                float dx0 = 0.f, dy0 = 0.f;
+                if (act) {
+                    kc = s_k[ek];
+                    const float4 a = s_a[ek];
+                    dx0 = a.x - bpx0;
+                    dy0 = a.y - bpy0;
+                }
+                float acc[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) acc[i] = 0.f;
+                const float2* row = sm + be * kEpPitch + 16 * bh;
+                const float4* gpx = s_gp[wp] + 16 * bh;
+#pragma unroll 4
+                for (int pp = 0; pp < 16; ++pp) {
+                    const float2 m = row[pp];
+                    const float4 gp = gpx[pp];
+                    const float dx = dx0 - (float)(pp & 7), dy = dy0 - (float)(pp >> 3);
+                    const float qx = m.x * dx, qdy = m.x * dy;
+                    acc[0] = fmaf(kc.x, qx, fmaf(kc.y, qdy, acc[0]));
+                    acc[1] = fmaf(kc.y, qx, fmaf(kc.z, qdy, acc[1]));
+                    acc[2] = fmaf(qx, dx, acc[2]);
+                    acc[3] = fmaf(qx, dy, acc[3]);
+                    acc[4] = fmaf(qdy, dy, acc[4]);
+                    acc[5] += m.x;
+                    acc[6] = fmaf(m.y, gp.x, acc[6]);
+                    acc[7] = fmaf(m.y, gp.y, acc[7]);
+                    acc[8] = fmaf(m.y, gp.z, acc[8]);
+                }
+#pragma unroll
+                for (int i = 0; i < 9; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 16);
+                if (act && bh == 0) {
+                    float4* gq = grad2d + 3 * (size_t)s_g[ek];
+                    atomicAdd(gq, make_float4(-acc[0], -acc[1], -0.5f * acc[2], -acc[3]));
+                    atomicAdd(gq + 1, make_float4(-0.5f * acc[4], acc[5] * kc.w, acc[6], acc[7]));
+                    atomicAdd((float*)(gq + 2), acc[8]);
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+    }  // work items
+}
+
 }  // namespace dg
 
 static dg::RViews make_rviews(const dg_camera* cams, int n, int B, const dg_raster_opts* o)
@@ -1005,10 +1219,25 @@ static dg_status launch_fwd(const float* feat, const uint32_t* gid, const uint32
     return DG_OK;
 }
 
+// Backward of 8x8 tiles, one pixel per thread: entry-parallel gradient sums
+// (k_render_bwd_ep) unless DG_BWD_EP is defined to 0.
+#ifndef DG_BWD_EP
+#define DG_BWD_EP 1
+#endif
+
 template <int B, int PPT, int REC>
 static void launch_bwd(const float* feat, const uint32_t* gid, const uint32_t* ranges, const dg::RViews& rv,
                        const RenderWs& w, const float* T, const int* last, const float* dL, float* g2, cudaStream_t s)
 {
+    if (DG_BWD_EP && B == 8 && PPT == 1) {
+        auto kep = dg::k_render_bwd_ep<REC>;
+        const int grid = resident_ctas(kep, 64);
+        cudaMemsetAsync(&w.hdr->cnt_bwd, 0, sizeof(int), s);
+        kep<<<grid, 64, 0, s>>>((const void*)feat, gid, (const uint2*)ranges, rv, w.hdr, w.items, w.sl, w.flags,
+                                w.flags_cap, T, last, dL, (float4*)g2);
+        dg_note_launch();
+        return;
+    }
     auto kern = dg::k_render_bwd<B, PPT, REC>;
     const int grid = resident_ctas(kern, B * B / PPT);
     cudaMemsetAsync(&w.hdr->cnt_bwd, 0, sizeof(int), s);

@@ -444,10 +444,12 @@ class Trainer:
                     skipped_steps=self.skipped_steps)
 
 
-def make_dataset(n_gt, n_views, W, H, device, seed=1001):
-    """GT scene, cameras and GT renders; every 8th view held out."""
+def make_dataset(n_gt, n_views, W, H, device, seed=1001, gt=None):
+    """GT scene (generated, or the given one), cameras and GT renders; every
+    8th view held out."""
     from . import synth
-    gt = synth.textured_scene(n_gt, seed)
+    if gt is None:
+        gt = synth.textured_scene(n_gt, seed)
     cams = synth.ring_cameras(n_views, W, H, 5.0, seed + 1000)
     rz = Rasterizer(device, capi.raster_opts())
     gtp = torch.from_numpy(np.ascontiguousarray(gt.T)).to(device)

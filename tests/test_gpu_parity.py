@@ -644,16 +644,23 @@ def test_fullsize_sampled_tiles_and_pixels(fullsize):
     np.testing.assert_array_equal(G.np_(rz.examined)[py, px], o["examined"])
 
 
-def test_fullsize_backward_on_sampled_tiles(fullsize):
+@pytest.mark.parametrize("tile", [16, 8])
+def test_fullsize_backward_on_sampled_tiles(fullsize, tile):
+    """The bench's view (tile 16, and tile 8, the bench's launch shape with the
+    entry-parallel backward) on tiles of 16x16 pixels with dL/dimg set."""
     model, view, rz, params, gcam, fr = fullsize
     P, W, H = model.shape[0], 1237, 822
+    if tile != 16:
+        rz = Rasterizer("cuda", capi.raster_opts(tile=tile))
+        fr = rz.forward(params, P, gcam)
+        torch.cuda.synchronize()
     rec = _records(rz, P)
     gid, ranges = _gpu_bins(rz, fr)
-    # dL/dimg non-zero only on a few tiles: the oracle's adjoint then touches only them
+    # dL/dimg non-zero only on a few 16x16 blocks: the oracle's adjoint then touches only them
     rng = np.random.default_rng(8)
     dL = np.zeros((3, H, W), np.float32)
-    TX = (W + 15) // 16
-    for t in rng.choice(ranges.shape[0], 6, replace=False):
+    TX, TY = (W + 15) // 16, (H + 15) // 16
+    for t in rng.choice(TX * TY, 6, replace=False):
         ty, tx = divmod(int(t), TX)
         ys, xs = slice(ty * 16, min(H, ty * 16 + 16)), slice(tx * 16, min(W, tx * 16 + 16))
         hh, ww = ys.stop - ys.start, xs.stop - xs.start
@@ -662,7 +669,8 @@ def test_fullsize_backward_on_sampled_tiles(fullsize):
     rz.backward(params, fr, torch.from_numpy(dL).cuda(), grads)
     torch.cuda.synchronize()
     g2 = G.np_(rz.grad2d[:P])[:, :9]
-    og2 = oracle.render_bwd(rec["feat"], W, H, 16, gid, ranges, np.zeros(3), oracle.consts(), dL.astype(np.float64))
+    og2 = oracle.render_bwd(rec["feat"], W, H, tile, gid, ranges, np.zeros(3), oracle.consts(tile=tile),
+                            dL.astype(np.float64))
     # same dL normalisation and tolerance as the 64x64 cases (1e-4 relative, 1e-6 absolute)
     ok, worst, nbad = G.grad_close(g2, og2)
     assert ok, (worst, nbad)
