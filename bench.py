@@ -47,6 +47,10 @@ TRAIN_RUNS = ("plain", "scheduled:a=2:v=16:graph=1:record=mixed", "scheduled:a=4
 FLOPS_TEST = 12
 FLOPS_FWD_BLEND = 7
 FLOPS_BWD_BLEND = 38
+# the same passes counted per examined entry as the hot-path scope table does
+# (forward about 18 FP32 operations per examined entry, backward about 50)
+FLOPS_FWD_PER_E = 18
+FLOPS_BWD_PER_E = 50
 SM_COUNT, FP32_LANES, MAX_MHZ = 152, 128, 2070.0
 
 
@@ -463,6 +467,27 @@ def run_ours(args):
         out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                            "frac": round(ach / hbm, 4), "traffic": measured_traffic(dom),
                            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s"}
+    # every timed stage against its bound: HBM stages by algorithmic bytes, the
+    # compositing passes by FP32 work (both counts: the per-examined-entry count
+    # and the count of the operations the algorithm needs per walked/blended entry)
+    alu_peak = SM_COUNT * FP32_LANES * 2 * MAX_MHZ * 1e6 / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    by_stage = {}
+    for k, st in stages.items():
+        dur = st["ms"] * 1e-3
+        if dur <= 0 or k not in work:
+            continue
+        kind_k, units_k = work[k]
+        if kind_k == "alu":
+            per_e = {"render_fwd": FLOPS_FWD_PER_E * pf, "render_bwd": FLOPS_BWD_PER_E * pf}[k]
+            by_stage[k] = {"bound": "alu", "unit": "TFLOP/s", "peak": round(alu_peak, 2),
+                           "achieved": round(units_k / dur / 1e12, 3), "frac": round(units_k / dur / 1e12 / alu_peak, 4),
+                           "achieved_per_examined_count": round(per_e / dur / 1e12, 3),
+                           "frac_per_examined_count": round(per_e / dur / 1e12 / alu_peak, 4)}
+        else:
+            by_stage[k] = {"bound": "hbm", "unit": "GB/s", "peak": hbm_peak,
+                           "achieved": round(units_k / dur / 1e9, 1), "frac": round(units_k / dur / 1e9 / hbm_peak, 4)}
+    out["roofline_by_stage"] = by_stage
     out["work"] = {"pairs_per_view": int(sum(M_tot) / len(M_tot)), "examined_per_view": int(pf),
                    "walked_back_per_view": int(pl), "blended_per_view": int(pb)}
     # the rasterizer's forward and backward: projection, binning, both compositing passes

@@ -472,6 +472,8 @@ def main(argv=None):
     ap.add_argument("--gamma", type=float, default=0.98, help="Eq. 5 momentum")
     ap.add_argument("--iters", type=int, default=30000, help="views rendered (steps x views per step)")
     ap.add_argument("--n-gt", type=int, default=2_000_000)
+    ap.add_argument("--seed", type=int, default=1001,
+                    help="scene seed (cameras seed + 1000); 1000 + k for configuration k")
     ap.add_argument("--n-init", type=int, default=100_000)
     ap.add_argument("--views", type=int, default=160)
     ap.add_argument("--width", type=int, default=1237)
@@ -493,7 +495,7 @@ def main(argv=None):
     args = ap.parse_args(argv)
     from . import synth
     dev = torch.device("cuda")
-    gt, cams, imgs, train, test = make_dataset(args.n_gt, args.views, args.width, args.height, dev)
+    gt, cams, imgs, train, test = make_dataset(args.n_gt, args.views, args.width, args.height, dev, seed=args.seed)
     init = synth.perturb(gt, 3001, n_keep=args.n_init)
     runs = args.runs or {"both": ["plain", "scheduled"],
                          "all": ["plain", "scheduled", "reso", "prim"]}.get(args.arm, [args.arm])
