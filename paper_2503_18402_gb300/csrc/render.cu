@@ -1038,7 +1038,13 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
             }
             const uint32_t used = __reduce_or_sync(0xffffffffu, mine);
             __syncwarp();
-            // B: entry kb + be over pixels 16 bh .. 16 bh + 15 of the warp
+            // B: entry kb + be over pixels 16 bh .. 16 bh + 15 of the warp (an 8x2
+            // block).  The sums over pixels of dp dx, dp dy, dp dx^2, dp dx dy,
+            // dp dy^2 (dx, dy: Gaussian centre minus pixel centre) follow from
+            // moments of dp about the block's centre, whose pixel offsets are
+            // compile-time constants: per row, sum dp and sum dp ox; sum dp ox^2
+            // (ox in -3.5 .. 3.5, oy = -0.5 / +0.5).  Taking the block's own
+            // centre keeps the expansion free of large cancellations.
             if (used) {
                 const int ek = kb + be;
                 const bool act = ek < ke && ((used >> be) & 1u);
@@ -1047,30 +1053,44 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                 if (act) {
                     kc = s_k[ek];
                     const float4 a = s_a[ek];
-                    dx0 = a.x - bpx0;
-                    dy0 = a.y - bpy0;
+                    dx0 = a.x - (bpx0 + 3.5f);  // Gaussian centre relative to the block centre
+                    dy0 = a.y - (bpy0 + 0.5f);
                 }
-                float acc[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) acc[i] = 0.f;
+                float s0a = 0.f, s0b = 0.f, sxa = 0.f, sxb = 0.f, sxx = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
                 const float2* row = sm + be * kEpPitch + 16 * bh;
                 const float4* gpx = s_gp[wp] + 16 * bh;
-#pragma unroll 4
-                for (int pp = 0; pp < 16; ++pp) {
-                    const float2 m = row[pp];
-                    const float4 gp = gpx[pp];
-                    const float dx = dx0 - (float)(pp & 7), dy = dy0 - (float)(pp >> 3);
-                    const float qx = m.x * dx, qdy = m.x * dy;
-                    acc[0] = fmaf(kc.x, qx, fmaf(kc.y, qdy, acc[0]));
-                    acc[1] = fmaf(kc.y, qx, fmaf(kc.z, qdy, acc[1]));
-                    acc[2] = fmaf(qx, dx, acc[2]);
-                    acc[3] = fmaf(qx, dy, acc[3]);
-                    acc[4] = fmaf(qdy, dy, acc[4]);
-                    acc[5] += m.x;
-                    acc[6] = fmaf(m.y, gp.x, acc[6]);
-                    acc[7] = fmaf(m.y, gp.y, acc[7]);
-                    acc[8] = fmaf(m.y, gp.z, acc[8]);
+                // the block's two rows of 8 pixels (first row: oy = -0.5, second: +0.5)
+#pragma unroll 1
+                for (int r = 0; r < 2; ++r) {
+                    float s0 = 0.f, sx = 0.f;
+#pragma unroll
+                    for (int px = 0; px < 8; ++px) {
+                        const float2 m = row[8 * r + px];
+                        const float4 gp = gpx[8 * r + px];
+                        const float ox = (float)px - 3.5f;
+                        s0 += m.x;
+                        sx = fmaf(m.x, ox, sx);
+                        sxx = fmaf(m.x, ox * ox, sxx);
+                        c0 = fmaf(m.y, gp.x, c0);
+                        c1 = fmaf(m.y, gp.y, c1);
+                        c2 = fmaf(m.y, gp.z, c2);
+                    }
+                    if (r == 0) { s0a = s0; sxa = sx; } else { s0b = s0; sxb = sx; }
                 }
+                // moments about the block centre, then the sums for dx = dx0 - ox, dy = dy0 - oy
+                const float S0 = s0a + s0b, Sx = sxa + sxb, Sy = 0.5f * (s0b - s0a), Sxy = 0.5f * (sxb - sxa);
+                const float Syy = 0.25f * S0;
+                const float qx = fmaf(dx0, S0, -Sx), qy = fmaf(dy0, S0, -Sy);  // sum dp dx, sum dp dy
+                float acc[9];
+                acc[0] = fmaf(kc.x, qx, kc.y * qy);
+                acc[1] = fmaf(kc.y, qx, kc.z * qy);
+                acc[2] = fmaf(dx0, fmaf(dx0, S0, -2.f * Sx), sxx);                      // sum dp dx^2
+                acc[3] = fmaf(dx0, fmaf(dy0, S0, -Sy), fmaf(-dy0, Sx, Sxy));           // sum dp dx dy
+                acc[4] = fmaf(dy0, fmaf(dy0, S0, -2.f * Sy), Syy);                      // sum dp dy^2
+                acc[5] = S0;
+                acc[6] = c0;
+                acc[7] = c1;
+                acc[8] = c2;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 16);
                 if (act && bh == 0) {
