@@ -339,6 +339,26 @@ __device__ inline Item next_item(int* counter, int count, const int4* list, cons
     return it;
 }
 
+// Per-pair blend flag written by the forward: 0 when no pixel of the item
+// blended the entry; otherwise bit w set when a pixel of warp w's block did.
+// With 8x8 tiles and one pixel per thread (two warps of 8x4 pixels, the
+// layout of k_render_bwd_ep) bit 7 marks that the low bits are per-warp bits
+// of that layout; other layouts set bit 0 only.
+constexpr uint8_t kFlagWarpBits = 0x80;
+template <int B, int PPT, int NW, int NS>
+__device__ inline uint8_t blend_flag(const uint8_t (&s_bl)[NW][NS], int slot)
+{
+    uint8_t f = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) f |= s_bl[w][slot] ? 1 : 0;
+    if (B == 8 && PPT == 1 && f) {
+        f = kFlagWarpBits;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) f |= s_bl[w][slot] ? (uint8_t)(1u << w) : 0;
+    }
+    return f;
+}
+
 // Compositing of one work item.  PROD: pass 1 of a split tile (product of
 // the chunk's (1 - alpha) factors from 1, no colour).  Otherwise Eq. 1 over
 // the item's entries from T_in, writing the final pixels (whole tile) or the
@@ -356,7 +376,10 @@ k_render_fwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
     __shared__ float4 s_a[NT];    // u, v, a', b'  (prescaled conic, see below)
     __shared__ float2 s_q[NT];    // c', log2 o
     __shared__ float4 s_col[NT];  // r, g, b, list position (int bits)
-    __shared__ uint8_t s_bl[NT];  // staged entry blended by some pixel of the item
+    // staged entry blended by some pixel of warp w's block (one row per warp, no
+    // two warps write the same byte)
+    constexpr int NW = NT / 32;
+    __shared__ uint8_t s_bl[NW][NT];
     __shared__ int s_w[NT / 32];
     __shared__ int4 s_item;
     const bool planned = hdr->planned != 0 && items != nullptr;
@@ -409,7 +432,7 @@ k_render_fwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
     auto write_flags = [&]() {
         if (PROD || !flags || pj < 0) return;
         const long long gj = (long long)rg.x + pj;
-        if (pj < hi && gj < flags_cap) flags[gj] = pkeep ? s_bl[pslot] : 0;
+        if (pj < hi && gj < flags_cap) flags[gj] = pkeep ? blend_flag<B, PPT>(s_bl, pslot) : 0;
     };
     for (int base = lo; base < hi; base += NT) {
         if (__syncthreads_count(alldone) == NT) break;
@@ -430,7 +453,8 @@ k_render_fwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
             s_a[slot] = make_float4(ga.x, ga.y, -0.5f * kLog2e * ga.z, -kLog2e * ga.w);
             s_q[slot] = make_float2(-0.5f * kLog2e * gb.x, __log2f(gb.y));
             s_col[slot] = make_float4(gb.z, gb.w, gc, __int_as_float(j));
-            s_bl[slot] = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) s_bl[w][slot] = 0;
         }
         __syncthreads();
         // Eq. 1 for entry kk at the thread's pixel k, given the entry's power p
@@ -453,7 +477,7 @@ k_render_fwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                     c2[k] += w * col.z;
                     last[k] = pos + 1;
                     ++nbl[k];
-                    s_bl[kk] = 1;
+                    s_bl[threadIdx.x >> 5][kk] = 1;
                 }
                 T[k] = Tn;
             }
@@ -896,6 +920,7 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
 // the warp's own pixels, so only the staging needs the CTA barrier.  The
 // opacity term uses d alpha / d o = alpha / o below the clamp: sum(dp) / o.
 constexpr int kEpG = 16;
+__device__ __forceinline__ long long gj_of(const uint2& rg, int j) { return (long long)rg.x + j; }
 constexpr int kEpPitch = 33;  // float2 per entry row of the (entry, pixel) matrix: 32 pixels + 1
 
 template <int REC>
@@ -913,6 +938,7 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
     __shared__ float4 s_col[NT];  // r, g, b, list position (int bits)
     __shared__ uint32_t s_g[NT];
     __shared__ float2 s_m[2][kEpG * kEpPitch];  // per warp: [entry][pixel] (dp, wT)
+    __shared__ uint8_t s_fl[NT];                 // staged entry: bit w = some pixel of warp w blends it
     __shared__ float4 s_gp[2][32];               // per warp: dL/dC of its pixels
     __shared__ int s_w[NT / 32];
     __shared__ int s_n;
@@ -996,25 +1022,43 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
             s_q[slot] = make_float2(-0.5f * kLog2e * gb.x, __log2f(gb.y));
             s_k[slot] = make_float4(ga.z, ga.w, gb.x, __frcp_rn(gb.y));
             s_col[slot] = make_float4(gb.z, gb.w, gc, __int_as_float(j));
+            // which warps' pixels blend the entry: the forward's per-warp bits when it
+            // ran with this layout, else both
+            const uint8_t f = (flags && gj_of(rg, j) < flags_cap) ? flags[gj_of(rg, j)] : 0;
+            s_fl[slot] = (f & kFlagWarpBits) ? (uint8_t)(f & 3u) : (uint8_t)3u;
         }
         __syncthreads();
         for (int kb = ((cnt - 1) / kEpG) * kEpG; kb >= 0 && cnt > 0; kb -= kEpG) {
             const int ke = min(cnt, kb + kEpG);
-            // A: this lane's pixel over the group's entries, back to front, four at a time
+            // A: this lane's pixel over the group's entries that some pixel of this
+            // warp blends, back to front, four at a time.  (An entry no pixel of the
+            // warp blends has no gradient from these pixels and leaves their T and
+            // g . S unchanged; its row of the matrix is not written and phase B
+            // does not use it.)
+            uint32_t todo = __ballot_sync(0xffffffffu, lane < ke - kb && ((s_fl[kb + min(lane, kEpG - 1)] >> wp) & 1u));
             uint32_t mine = 0;  // entries of the group this pixel blends (bit kk - kb)
-            for (int k0 = ke - 1; k0 >= kb; k0 -= 4) {
+            while (todo) {
+                int kk4[4];
+                bool val[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    val[u] = todo != 0;
+                    const int b = val[u] ? 31 - __clz(todo) : 0;
+                    kk4[u] = kb + b;
+                    todo &= ~(1u << b);
+                }
                 float al[4], iv[4], gcl[4];
                 bool bl[4], un[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int kk = k0 - u >= kb ? k0 - u : kb;
+                    const int kk = kk4[u];
                     const float4 col = s_col[kk];
                     const float4 a = s_a[kk];
                     const float2 q = s_q[kk];
                     const float dx = a.x - pxc, dy = a.y - pyc;
                     const float p = fmaf(dx, fmaf(a.w, dy, a.z * dx), q.x * dy * dy);
                     const float e = p + q.y;
-                    bl[u] = k0 - u >= kb && __float_as_int(col.w) < lastp && p <= 0.f && e >= kLog2AlphaMin;
+                    bl[u] = val[u] && __float_as_int(col.w) < lastp && p <= 0.f && e >= kLog2AlphaMin;
                     const float raw = ex2_approx(e);
                     al[u] = fminf(kAlphaMax, raw);
                     un[u] = raw <= kAlphaMax;
@@ -1023,7 +1067,7 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    if (k0 - u < kb) break;
+                    if (!val[u]) break;
                     float dpv = 0.f, wTv = 0.f;
                     if (bl[u]) {
                         T *= iv[u];
@@ -1031,9 +1075,9 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                         const float dLda = fmaf(T, gcl[u], -gS * iv[u]);
                         gS = fmaf(wTv, gcl[u], gS);
                         dpv = un[u] ? dLda * al[u] : 0.f;
-                        mine |= 1u << (k0 - u - kb);
+                        mine |= 1u << (kk4[u] - kb);
                     }
-                    sm[(k0 - u - kb) * kEpPitch + lane] = make_float2(dpv, wTv);
+                    sm[(kk4[u] - kb) * kEpPitch + lane] = make_float2(dpv, wTv);
                 }
             }
             const uint32_t used = __reduce_or_sync(0xffffffffu, mine);

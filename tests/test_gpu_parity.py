@@ -891,3 +891,34 @@ def test_backward_with_and_without_blend_flags():
     ok, worst, nbad = G.grad_close(out[0], out[1])
     assert ok, (worst, nbad)
     assert np.abs(out[0]).max() > 0
+
+
+@pytest.mark.parametrize("ppt_fwd", [1, 2])
+def test_tile8_backward_with_per_warp_flags_and_fallback(ppt_fwd):
+    """At 8x8 tiles with one pixel per thread the forward writes, per pair,
+    which 8x4 block blended the entry, and the backward's warps walk only
+    their own block's entries; after a forward at another launch shape (two
+    pixels per thread) the flags carry no block bits and every warp walks
+    every flagged entry.  Both match the oracle's adjoint (bg != 0, ragged)."""
+    g = synth.random_gaussians(6000, 321)
+    g[:, 3:6] += 0.25
+    W, H = 117, 83
+    cam = synth.camera_cfg0(W, H, 4.0)
+    bg = (0.2, 0.4, 0.1)
+    opts = capi.raster_opts(tile=8, bg=bg)
+    rz = Rasterizer("cuda", opts, ppt_fwd=ppt_fwd, ppt_bwd=1)
+    P = g.shape[0]
+    params = G.gpu_params(g)
+    fr = rz.forward(params, P, G.gpu_camera(cam))
+    torch.cuda.synchronize()
+    rec = _records(rz, P)
+    gid, ranges = _gpu_bins(rz, fr)
+    k = oracle.consts(tile=8)
+    rng = np.random.default_rng(ppt_fwd)
+    dL = (rng.normal(size=(3, H, W)) / (3 * H * W)).astype(np.float32)
+    rz.backward_render(fr, torch.from_numpy(dL).cuda())
+    torch.cuda.synchronize()
+    og2 = oracle.render_bwd(rec["feat"], W, H, 8, gid, ranges, G.f32(bg), k, dL.astype(np.float64))
+    ok, worst, nbad = G.grad_close(G.np_(rz.grad2d[:P])[:, :9], og2)
+    assert ok, (worst, nbad)
+    assert np.abs(og2).max() > 0
