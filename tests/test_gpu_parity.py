@@ -498,7 +498,7 @@ def test_adam_parity():
     np.testing.assert_array_equal(got[:, P:], p[:, P:])  # padding untouched
 
 
-@pytest.mark.parametrize("sh,V", [(3, 1), (3, 3), (1, 2)])
+@pytest.mark.parametrize("sh,V", [(3, 1), (2, 1), (0, 1), (3, 3), (1, 2)])
 def test_fused_project_bwd_adam_matches_two_calls(sh, V):
     """dg_project_bwd_adam = dg_project_bwd followed by dg_adam_step
     (including Gaussians culled in every view, whose moments still decay).
