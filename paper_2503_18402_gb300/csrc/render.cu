@@ -50,6 +50,7 @@
 // skip the entry, so it is dropped from the batch (stable compaction; the
 // original list position is kept for `last`).  Results are unchanged.
 #include <climits>
+#include <stdlib.h>
 #include <string.h>
 
 #include <cuda_bf16.h>
@@ -897,9 +898,45 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
     }  // work items
 }
 
-// Backward of 8x8 tiles with one pixel per thread (64 threads, two warps of
-// 8x4 pixels), with entry-parallel gradient sums.  A staged batch of up to 64
-// entries is taken in groups of kEpG = 16, back to front; per group, each warp:
+constexpr int kEpG = 16;
+constexpr int kEpPitch = 33;  // float2 per entry row of the (entry, pixel) matrix: 32 pixels + 1
+
+// Next work item of this warp: item index w covers tile (or chunk) w / 2 and
+// the 8x4 pixel block w % 2 of it; *blk receives the block.  Warp-uniform.
+__device__ inline Item next_item_warp(int* counter, int count, const int4* list, const RViews& rv, int* blk)
+{
+    int w = 0;
+    if ((threadIdx.x & 31) == 0) w = atomicAdd(counter, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    Item it;
+    it.tile = -1;
+    if (w >= 2 * count) return it;
+    const int i = w >> 1;
+    *blk = w & 1;
+    const int4 q = list ? list[i] : make_int4(i, 0, 1, -1);
+    it.tile = q.x; it.c = q.y; it.nch = q.z; it.slot0 = q.w;
+    int v = 0;
+    while (v + 1 < rv.n && it.tile >= rv.toff[v + 1]) ++v;
+    const int t = it.tile - rv.toff[v];
+    it.v = v;
+    it.tx = t % rv.TX[v];
+    it.ty = t / rv.TX[v];
+    it.W = rv.W[v];
+    it.H = rv.H[v];
+    it.poff = rv.poff[v];
+    return it;
+}
+
+// Backward of 8x8 tiles with one pixel per thread, entry-parallel gradient
+// sums, each warp on its own.  A work item is one 8x4 block of a tile (or of a
+// chunk of a split tile), taken by the warp from the shared counter; no
+// CTA-wide barrier, so the two blocks of a tile, whose lists and walks
+// differ, do not wait for each other.  The warp walks back from the largest
+// `last` of its own 32 pixels and stages, in batches of 32 candidates, only
+// the entries some pixel of its block blended (the forward's per-block bit,
+// or every flagged entry when the forward ran at another launch shape; the
+// block-rectangle alpha test when there are no flags).  Per group of 16
+// staged entries:
 //   A. pixel-parallel (lane = pixel): walks the group's entries back to front
 //      exactly as k_render_bwd (the forward's blend test bit for bit, T
 //      recovered through 1/(1 - alpha), dL/dalpha from the running g . S) and
@@ -907,22 +944,15 @@ k_render_bwd(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
 //      dp = dL/dpower and wT = alpha T (0, 0 where the pixel does not blend).
 //      Four entries at a time: their tests, alphas and reciprocals do not
 //      depend on the transmittance chain and are formed first;
-//   B. entry-parallel (lane = entry of the group, one of two halves of the
-//      warp's 32 pixels): sums over its 16 pixels the nine partial gradients
-//      formed from (dp, wT), the entry's conic, the pixel's offset and its
-//      dL/dC; the two halves are added with one shuffle each and the entry's
-//      sums go out with three vector atomics when some pixel of the warp
-//      blended it.
-// Phase B runs on full warps: the gradient arithmetic per blended (pixel,
-// entry) of k_render_bwd (about 40 instructions on the lanes that blend, then
-// a 12-shuffle reduction or up to 16 lanes of atomics) becomes about 17
-// instructions per (pixel, entry) slot on all lanes.  Both phases touch only
-// the warp's own pixels, so only the staging needs the CTA barrier.  The
-// opacity term uses d alpha / d o = alpha / o below the clamp: sum(dp) / o.
-constexpr int kEpG = 16;
-__device__ __forceinline__ long long gj_of(const uint2& rg, int j) { return (long long)rg.x + j; }
-constexpr int kEpPitch = 33;  // float2 per entry row of the (entry, pixel) matrix: 32 pixels + 1
-
+//   B. entry-parallel (lane = entry of the group, one of two 8x2 halves of the
+//      block): the sums over the half's pixels of dp dx, dp dy, dp dx^2,
+//      dp dx dy, dp dy^2 (dx, dy: Gaussian centre minus pixel centre) follow
+//      from moments of dp about the half's centre, whose pixel offsets are
+//      compile-time constants (per row sum dp and sum dp ox, and sum dp ox^2;
+//      ox in -3.5 .. 3.5, oy = -0.5 / +0.5; expanding about the half's own
+//      centre keeps cancellation small), plus the colour sums sum wT dL/dC;
+//      one shuffle adds the halves and three vector atomics per entry go out.
+// The opacity term uses d alpha / d o = alpha / o below the clamp: sum(dp) / o.
 template <int REC>
 __global__ void __launch_bounds__(64, 16)
 k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
@@ -931,35 +961,38 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                 const float* __restrict__ Tfin, const int* __restrict__ lastin,
                 const float* __restrict__ dLdimg, float4* __restrict__ grad2d)
 {
-    constexpr int B = 8, NT = 64, NPIX = 64;
-    __shared__ float4 s_a[NT];    // u, v, a', b'  (the forward's prescaled conic)
-    __shared__ float2 s_q[NT];    // c', log2 o
-    __shared__ float4 s_k[NT];    // A, B, C, 1/o
-    __shared__ float4 s_col[NT];  // r, g, b, list position (int bits)
-    __shared__ uint32_t s_g[NT];
+    constexpr int B = 8, NPIX = 64;
+    __shared__ float4 s_a[2][32];    // u, v, a', b'  (the forward's prescaled conic)
+    __shared__ float2 s_q[2][32];    // c', log2 o
+    __shared__ float4 s_k[2][32];    // A, B, C, 1/o
+    __shared__ float4 s_col[2][32];  // r, g, b, list position (int bits)
+    __shared__ uint32_t s_g[2][32];
     __shared__ float2 s_m[2][kEpG * kEpPitch];  // per warp: [entry][pixel] (dp, wT)
-    __shared__ uint8_t s_fl[NT];                 // staged entry: bit w = some pixel of warp w blends it
     __shared__ float4 s_gp[2][32];               // per warp: dL/dC of its pixels
-    __shared__ int s_w[NT / 32];
-    __shared__ int s_n;
-    __shared__ int4 s_item;
     const float bg0 = rv.bg0, bg1 = rv.bg1, bg2 = rv.bg2;
     const bool planned = hdr->planned != 0 && items != nullptr;
     const int L = planned ? hdr->L : INT_MAX;
     const int count = planned ? hdr->n_items : rv.total;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     float2* sm = s_m[wp];
+    float4* wa = s_a[wp];
+    float2* wq = s_q[wp];
+    float4* wk = s_k[wp];
+    float4* wc = s_col[wp];
+    uint32_t* wg = s_g[wp];
+    const uint32_t lt = (1u << lane) - 1u;
     for (;;) {
-    const Item it = next_item(&hdr->cnt_bwd, count, planned ? items : nullptr, rv, &s_item);
+    int blk = 0;
+    const Item it = next_item_warp(&hdr->cnt_bwd, count, planned ? items : nullptr, rv, &blk);
     if (it.tile < 0) break;
     const int tile = it.tile, tx = it.tx, ty = it.ty, W = it.W, H = it.H;
-    int lx, ly0;
-    pix_of<B, 1>(threadIdx.x, &lx, &ly0);
+    const int lx = lane & 7, ly0 = 4 * blk + (lane >> 3);
     const int x = tx * B + lx;
     const int y = ty * B + ly0;
     const float pxc = (float)x + 0.5f, pyc = (float)y + 0.5f;
-    const float tpx0 = (float)(tx * B) + 0.5f, tpx1 = tpx0 + (float)(B - 1);
-    const float tpy0 = (float)(ty * B) + 0.5f, tpy1 = tpy0 + (float)(B - 1);
+    // this block's pixel centres: [bx0, bx1] x [by0, by1]
+    const float bx0 = (float)(tx * B) + 0.5f, bx1 = bx0 + 7.f;
+    const float by0 = (float)(ty * B + 4 * blk) + 0.5f, by1 = by0 + 3.f;
     const uint2 rg = ranges[tile];
     const int nlist = (int)(rg.y - rg.x);
     const bool split = it.slot0 >= 0;
@@ -976,26 +1009,23 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
         g1 = dl[HW + pix];
         g2 = dl[2 * HW + pix];
         if (split) {
-            const size_t s = (size_t)(it.slot0 + it.c) * NPIX + (size_t)(ly0 * B + lx);
-            T = sl.tout[s];
-            gS = g0 * sl.c0[s] + g1 * sl.c1[s] + g2 * sl.c2[s];
+            const size_t sidx = (size_t)(it.slot0 + it.c) * NPIX + (size_t)(ly0 * B + lx);
+            T = sl.tout[sidx];
+            gS = g0 * sl.c0[sidx] + g1 * sl.c1[sidx] + g2 * sl.c2[sidx];
         } else {
             T = Tfin[it.poff + pix];
             gS = T * (g0 * bg0 + g1 * bg1 + g2 * bg2);
         }
     }
     s_gp[wp][lane] = make_float4(g0, g1, g2, 0.f);
-    if (threadIdx.x == 0) s_n = 0;
-    __syncthreads();
-    if (lastp > 0) atomicMax(&s_n, lastp);
-    __syncthreads();
-    const int top = min(s_n, hi);
-    // phase B: this lane's entry of the group and half of the warp's pixels
-    // (pixels 16 h .. 16 h + 15 = rows 2h, 2h + 1 of the warp's 8x4 block)
+    const int top = min(__reduce_max_sync(0xffffffffu, lastp), hi);
+    // phase B: this lane's entry of the group and half of the block's pixels
+    // (pixels 16 h .. 16 h + 15 = rows 2h, 2h + 1 of the block)
     const int be = lane & (kEpG - 1), bh = lane >> 4;
-    const float bpx0 = tpx0, bpy0 = tpy0 + (float)(4 * wp + 2 * bh);
-    for (int base = top > lo ? lo + ((top - lo - 1) / NT) * NT : lo - 1; base >= lo; base -= NT) {
-        const int j = base + (int)threadIdx.x;
+    const float bpx0 = bx0, bpy0 = by0 + (float)(2 * bh);
+    __syncwarp();
+    for (int base = top > lo ? lo + ((top - lo - 1) / 32) * 32 : lo - 1; base >= lo; base -= 32) {
+        const int j = base + lane;
         bool keep = false;
         float4 ga, gb;
         float gc = 0.f;
@@ -1003,7 +1033,8 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
         if (j < top) {
             const long long gj = (long long)rg.x + j;
             if (flags && gj < flags_cap) {
-                keep = flags[gj] != 0;
+                const uint8_t f = flags[gj];
+                keep = (f & kFlagWarpBits) ? ((f >> blk) & 1u) != 0 : f != 0;
                 if (keep) {
                     g = gid[gj];
                     load_record<REC>(feat, g, ga, gb, gc);
@@ -1011,54 +1042,37 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
             } else {
                 g = gid[gj];
                 load_record<REC>(feat, g, ga, gb, gc);
-                keep = !tile_skip(ga, gb, tpx0, tpx1, tpy0, tpy1);
+                keep = !tile_skip(ga, gb, bx0, bx1, by0, by1);
             }
         }
-        int cnt;
-        const int slot = compact_index<NT>(keep, s_w, &cnt);
+        const uint32_t km = __ballot_sync(0xffffffffu, keep);
+        const int cnt = __popc(km);
         if (keep) {
-            s_g[slot] = g;
-            s_a[slot] = make_float4(ga.x, ga.y, -0.5f * kLog2e * ga.z, -kLog2e * ga.w);
-            s_q[slot] = make_float2(-0.5f * kLog2e * gb.x, __log2f(gb.y));
-            s_k[slot] = make_float4(ga.z, ga.w, gb.x, __frcp_rn(gb.y));
-            s_col[slot] = make_float4(gb.z, gb.w, gc, __int_as_float(j));
-            // which warps' pixels blend the entry: the forward's per-warp bits when it
-            // ran with this layout, else both
-            const uint8_t f = (flags && gj_of(rg, j) < flags_cap) ? flags[gj_of(rg, j)] : 0;
-            s_fl[slot] = (f & kFlagWarpBits) ? (uint8_t)(f & 3u) : (uint8_t)3u;
+            const int slot = __popc(km & lt);
+            wg[slot] = g;
+            wa[slot] = make_float4(ga.x, ga.y, -0.5f * kLog2e * ga.z, -kLog2e * ga.w);
+            wq[slot] = make_float2(-0.5f * kLog2e * gb.x, __log2f(gb.y));
+            wk[slot] = make_float4(ga.z, ga.w, gb.x, __frcp_rn(gb.y));
+            wc[slot] = make_float4(gb.z, gb.w, gc, __int_as_float(j));
         }
-        __syncthreads();
+        __syncwarp();
         for (int kb = ((cnt - 1) / kEpG) * kEpG; kb >= 0 && cnt > 0; kb -= kEpG) {
             const int ke = min(cnt, kb + kEpG);
-            // A: this lane's pixel over the group's entries that some pixel of this
-            // warp blends, back to front, four at a time.  (An entry no pixel of the
-            // warp blends has no gradient from these pixels and leaves their T and
-            // g . S unchanged; its row of the matrix is not written and phase B
-            // does not use it.)
-            uint32_t todo = __ballot_sync(0xffffffffu, lane < ke - kb && ((s_fl[kb + min(lane, kEpG - 1)] >> wp) & 1u));
-            uint32_t mine = 0;  // entries of the group this pixel blends (bit kk - kb)
-            while (todo) {
-                int kk4[4];
-                bool val[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    val[u] = todo != 0;
-                    const int b = val[u] ? 31 - __clz(todo) : 0;
-                    kk4[u] = kb + b;
-                    todo &= ~(1u << b);
-                }
+            // A: this lane's pixel over the group's entries, back to front, four at a time
+            uint32_t mine = 0;
+            for (int k0 = ke - 1; k0 >= kb; k0 -= 4) {
                 float al[4], iv[4], gcl[4];
                 bool bl[4], un[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int kk = kk4[u];
-                    const float4 col = s_col[kk];
-                    const float4 a = s_a[kk];
-                    const float2 q = s_q[kk];
+                    const int kk = k0 - u >= kb ? k0 - u : kb;
+                    const float4 col = wc[kk];
+                    const float4 a = wa[kk];
+                    const float2 q = wq[kk];
                     const float dx = a.x - pxc, dy = a.y - pyc;
                     const float p = fmaf(dx, fmaf(a.w, dy, a.z * dx), q.x * dy * dy);
                     const float e = p + q.y;
-                    bl[u] = val[u] && __float_as_int(col.w) < lastp && p <= 0.f && e >= kLog2AlphaMin;
+                    bl[u] = k0 - u >= kb && __float_as_int(col.w) < lastp && p <= 0.f && e >= kLog2AlphaMin;
                     const float raw = ex2_approx(e);
                     al[u] = fminf(kAlphaMax, raw);
                     un[u] = raw <= kAlphaMax;
@@ -1067,7 +1081,7 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    if (!val[u]) break;
+                    if (k0 - u < kb) break;
                     float dpv = 0.f, wTv = 0.f;
                     if (bl[u]) {
                         T *= iv[u];
@@ -1075,35 +1089,27 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                         const float dLda = fmaf(T, gcl[u], -gS * iv[u]);
                         gS = fmaf(wTv, gcl[u], gS);
                         dpv = un[u] ? dLda * al[u] : 0.f;
-                        mine |= 1u << (kk4[u] - kb);
+                        mine |= 1u << (k0 - u - kb);
                     }
-                    sm[(kk4[u] - kb) * kEpPitch + lane] = make_float2(dpv, wTv);
+                    sm[(k0 - u - kb) * kEpPitch + lane] = make_float2(dpv, wTv);
                 }
             }
             const uint32_t used = __reduce_or_sync(0xffffffffu, mine);
             __syncwarp();
-            // B: entry kb + be over pixels 16 bh .. 16 bh + 15 of the warp (an 8x2
-            // block).  The sums over pixels of dp dx, dp dy, dp dx^2, dp dx dy,
-            // dp dy^2 (dx, dy: Gaussian centre minus pixel centre) follow from
-            // moments of dp about the block's centre, whose pixel offsets are
-            // compile-time constants: per row, sum dp and sum dp ox; sum dp ox^2
-            // (ox in -3.5 .. 3.5, oy = -0.5 / +0.5).  Taking the block's own
-            // centre keeps the expansion free of large cancellations.
             if (used) {
                 const int ek = kb + be;
                 const bool act = ek < ke && ((used >> be) & 1u);
                 float4 kc = make_float4(0.f, 0.f, 0.f, 0.f);
                 float dx0 = 0.f, dy0 = 0.f;
                 if (act) {
-                    kc = s_k[ek];
-                    const float4 a = s_a[ek];
-                    dx0 = a.x - (bpx0 + 3.5f);  // Gaussian centre relative to the block centre
+                    kc = wk[ek];
+                    const float4 a = wa[ek];
+                    dx0 = a.x - (bpx0 + 3.5f);
                     dy0 = a.y - (bpy0 + 0.5f);
                 }
                 float s0a = 0.f, s0b = 0.f, sxa = 0.f, sxb = 0.f, sxx = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
                 const float2* row = sm + be * kEpPitch + 16 * bh;
                 const float4* gpx = s_gp[wp] + 16 * bh;
-                // the block's two rows of 8 pixels (first row: oy = -0.5, second: +0.5)
 #pragma unroll 1
                 for (int r = 0; r < 2; ++r) {
                     float s0 = 0.f, sx = 0.f;
@@ -1121,16 +1127,15 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                     }
                     if (r == 0) { s0a = s0; sxa = sx; } else { s0b = s0; sxb = sx; }
                 }
-                // moments about the block centre, then the sums for dx = dx0 - ox, dy = dy0 - oy
                 const float S0 = s0a + s0b, Sx = sxa + sxb, Sy = 0.5f * (s0b - s0a), Sxy = 0.5f * (sxb - sxa);
                 const float Syy = 0.25f * S0;
-                const float qx = fmaf(dx0, S0, -Sx), qy = fmaf(dy0, S0, -Sy);  // sum dp dx, sum dp dy
+                const float qx = fmaf(dx0, S0, -Sx), qy = fmaf(dy0, S0, -Sy);
                 float acc[9];
                 acc[0] = fmaf(kc.x, qx, kc.y * qy);
                 acc[1] = fmaf(kc.y, qx, kc.z * qy);
-                acc[2] = fmaf(dx0, fmaf(dx0, S0, -2.f * Sx), sxx);                      // sum dp dx^2
-                acc[3] = fmaf(dx0, fmaf(dy0, S0, -Sy), fmaf(-dy0, Sx, Sxy));           // sum dp dx dy
-                acc[4] = fmaf(dy0, fmaf(dy0, S0, -2.f * Sy), Syy);                      // sum dp dy^2
+                acc[2] = fmaf(dx0, fmaf(dx0, S0, -2.f * Sx), sxx);
+                acc[3] = fmaf(dx0, fmaf(dy0, S0, -Sy), fmaf(-dy0, Sx, Sxy));
+                acc[4] = fmaf(dy0, fmaf(dy0, S0, -2.f * Sy), Syy);
                 acc[5] = S0;
                 acc[6] = c0;
                 acc[7] = c1;
@@ -1138,7 +1143,7 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
 #pragma unroll
                 for (int i = 0; i < 9; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 16);
                 if (act && bh == 0) {
-                    float4* gq = grad2d + 3 * (size_t)s_g[ek];
+                    float4* gq = grad2d + 3 * (size_t)wg[ek];
                     atomicAdd(gq, make_float4(-acc[0], -acc[1], -0.5f * acc[2], -acc[3]));
                     atomicAdd(gq + 1, make_float4(-0.5f * acc[4], acc[5] * kc.w, acc[6], acc[7]));
                     atomicAdd((float*)(gq + 2), acc[8]);
@@ -1146,8 +1151,8 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
             }
             __syncwarp();
         }
-        __syncthreads();
     }
+    __syncwarp();
     }  // work items
 }
 
@@ -1294,10 +1299,10 @@ static void launch_bwd(const float* feat, const uint32_t* gid, const uint32_t* r
                        const RenderWs& w, const float* T, const int* last, const float* dL, float* g2, cudaStream_t s)
 {
     if (DG_BWD_EP && B == 8 && PPT == 1) {
-        auto kep = dg::k_render_bwd_ep<REC>;
-        const int grid = resident_ctas(kep, 64);
+        auto kew = dg::k_render_bwd_ep<REC>;
+        const int grid = resident_ctas(kew, 64);
         cudaMemsetAsync(&w.hdr->cnt_bwd, 0, sizeof(int), s);
-        kep<<<grid, 64, 0, s>>>((const void*)feat, gid, (const uint2*)ranges, rv, w.hdr, w.items, w.sl, w.flags,
+        kew<<<grid, 64, 0, s>>>((const void*)feat, gid, (const uint2*)ranges, rv, w.hdr, w.items, w.sl, w.flags,
                                 w.flags_cap, T, last, dL, (float4*)g2);
         dg_note_launch();
         return;
