@@ -1156,6 +1156,162 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
     }  // work items
 }
 
+// Forward of 8x8 tiles with one pixel per thread, each warp on its own: a work
+// item is one 8x4 block of a tile (or of a chunk of a split tile), taken per
+// warp from the counter (the same compositing as k_render_fwd, pixel for
+// pixel and bit for bit).  The warp stages its block's candidates in batches
+// of 32 with the alpha test over the block's rectangle of pixel centres
+// (tighter than the tile's), stops as soon as its own 32 pixels are done, and
+// needs no CTA barrier.  Blend flags: the flag bytes are cleared before the
+// launch, and each entry some pixel of the block blended gets bit 7 and the
+// block's bit OR-ed into its byte (one 32-bit atomic OR per entry and block).
+template <bool PROD, int REC>
+__global__ void __launch_bounds__(64)
+k_render_fwd_w(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
+               const uint2* __restrict__ ranges, RViews rv, RHdr* hdr, const int4* __restrict__ items,
+               const int4* __restrict__ sitems, Slots sl, uint8_t* __restrict__ flags, long long flags_cap,
+               float* __restrict__ img, float* __restrict__ Tout, int* __restrict__ lastout,
+               int* __restrict__ exout, int* __restrict__ blout)
+{
+    constexpr int B = 8, NPIX = 64;
+    __shared__ float4 s_a[2][32];    // u, v, a', b'  (prescaled conic)
+    __shared__ float2 s_q[2][32];    // c', log2 o
+    __shared__ float4 s_col[2][32];  // r, g, b, list position (int bits)
+    const bool planned = hdr->planned != 0 && items != nullptr;
+    const int L = planned ? hdr->L : INT_MAX;
+    const int count = PROD ? hdr->n_slots : (planned ? hdr->n_items : rv.total);
+    const int4* list = PROD ? sitems : (planned ? items : nullptr);
+    int* counter = PROD ? &hdr->cnt_prod : &hdr->cnt_fwd;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    float4* wa = s_a[wp];
+    float2* wq = s_q[wp];
+    float4* wc = s_col[wp];
+    const uint32_t lt = (1u << lane) - 1u;
+    for (;;) {
+    int blk = 0;
+    const Item it = next_item_warp(counter, count, list, rv, &blk);
+    if (it.tile < 0) break;
+    if (PROD && it.c == it.nch - 1) continue;  // the last chunk's product is never needed
+    const int tile = it.tile, tx = it.tx, ty = it.ty, W = it.W, H = it.H;
+    const int lx = lane & 7, ly0 = 4 * blk + (lane >> 3);
+    const int x = tx * B + lx;
+    const int y = ty * B + ly0;
+    const float pxc = (float)x + 0.5f, pyc = (float)y + 0.5f;
+    const float bx0 = (float)(tx * B) + 0.5f, bx1 = bx0 + 7.f;
+    const float by0 = (float)(ty * B + 4 * blk) + 0.5f, by1 = by0 + 3.f;
+    const uint2 rg = ranges[tile];
+    const int n = (int)(rg.y - rg.x);
+    const bool split = it.slot0 >= 0;
+    const int lo = split ? it.c * L : 0;
+    const int hi = split ? (int)min((long long)n, (long long)lo + L) : n;
+    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+    int last = 0, stop = -1, nbl = 0;
+    bool done = !(x < W && y < H);
+    const int p = ly0 * B + lx;  // pixel within the tile
+    if (!PROD && split && it.c > 0) {
+        for (int c = 0; c < it.c; ++c) T *= sl.prod[(size_t)(it.slot0 + c) * NPIX + p];
+        if (T < kTMin) done = true;
+    }
+    bool alldone = __all_sync(0xffffffffu, done);
+    for (int base = lo; base < hi && !alldone; base += 32) {
+        const int j = base + lane;
+        bool keep = false;
+        float4 ga, gb;
+        float gc = 0.f;
+        if (j < hi) {
+            const uint32_t g = gid[rg.x + j];
+            load_record<REC>(feat, g, ga, gb, gc);
+            keep = !tile_skip(ga, gb, bx0, bx1, by0, by1);
+        }
+        const uint32_t km = __ballot_sync(0xffffffffu, keep);
+        const int cnt = __popc(km);
+        if (keep) {
+            const int slot = __popc(km & lt);
+            wa[slot] = make_float4(ga.x, ga.y, -0.5f * kLog2e * ga.z, -kLog2e * ga.w);
+            wq[slot] = make_float2(-0.5f * kLog2e * gb.x, __log2f(gb.y));
+            wc[slot] = make_float4(gb.z, gb.w, gc, __int_as_float(j));
+        }
+        __syncwarp();
+        uint32_t mine = 0;  // staged entries this pixel blended
+        auto blend = [&](int kk, float pw, float e) {
+            if (done || !(pw <= 0.f && e >= kLog2AlphaMin)) return;
+            const float alpha = fminf(kAlphaMax, ex2_approx(e));
+            const float Tn = fmaf(-alpha, T, T);
+            const float4 col = wc[kk];
+            const int pos = __float_as_int(col.w);
+            if (Tn < kTMin) {
+                done = true;
+                stop = pos;
+                if (PROD) T = Tn;
+            } else {
+                if (!PROD) {
+                    const float w = alpha * T;
+                    c0 += w * col.x;
+                    c1 += w * col.y;
+                    c2 += w * col.z;
+                    last = pos + 1;
+                    ++nbl;
+                    mine |= 1u << kk;
+                }
+                T = Tn;
+            }
+        };
+        for (int kk = 0; kk < cnt && !done; kk += kFwdUnroll) {
+            float pu[kFwdUnroll], eu[kFwdUnroll];
+#pragma unroll
+            for (int u = 0; u < kFwdUnroll; ++u) {
+                const int ku = kk + u < cnt ? kk + u : cnt - 1;
+                const float4 a = wa[ku];
+                const float2 q = wq[ku];
+                const float dx = a.x - pxc;
+                const float dy = a.y - pyc;
+                pu[u] = fmaf(dx, fmaf(a.w, dy, a.z * dx), q.x * dy * dy);
+                eu[u] = pu[u] + q.y;
+            }
+#pragma unroll
+            for (int u = 0; u < kFwdUnroll; ++u)
+                if (kk + u < cnt) blend(kk + u, pu[u], eu[u]);
+        }
+        if (!PROD && flags) {
+            const uint32_t bm = __reduce_or_sync(0xffffffffu, mine);
+            if (lane < cnt && ((bm >> lane) & 1u)) {
+                const long long gj = (long long)rg.x + __float_as_int(wc[lane].w);
+                if ((gj | 3) < flags_cap)
+                    atomicOr((unsigned int*)(flags + (gj & ~3ll)),
+                             (unsigned int)(kFlagWarpBits | (1u << blk)) << (8 * (int)(gj & 3)));
+            }
+        }
+        alldone = __all_sync(0xffffffffu, done);
+        __syncwarp();
+    }
+    if (split) {
+        const size_t s0 = (size_t)(it.slot0 + it.c) * NPIX + (size_t)p;
+        if (PROD) {
+            sl.prod[s0] = T;
+        } else {
+            sl.tout[s0] = T;
+            sl.c0[s0] = c0; sl.c1[s0] = c1; sl.c2[s0] = c2;
+            sl.last[s0] = last | (stop >= 0 ? kStopFlag : 0);
+            sl.nbl[s0] = nbl;
+            sl.stop[s0] = stop;
+        }
+        continue;
+    }
+    if (x < W && y < H) {
+        const size_t HW = (size_t)W * H;
+        float* im = img + 3 * it.poff;
+        const size_t pix = (size_t)y * W + x;
+        im[pix] = c0 + T * rv.bg0;
+        im[HW + pix] = c1 + T * rv.bg1;
+        im[2 * HW + pix] = c2 + T * rv.bg2;
+        Tout[it.poff + pix] = T;
+        lastout[it.poff + pix] = last;
+        if (exout) exout[it.poff + pix] = stop >= 0 ? stop + 1 : n;
+        if (blout) blout[it.poff + pix] = nbl;
+    }
+    }  // work items
+}
+
 }  // namespace dg
 
 static dg::RViews make_rviews(const dg_camera* cams, int n, int B, const dg_raster_opts* o)
@@ -1245,12 +1401,55 @@ static RenderWs render_ws_fixed(void* base, long long n_tiles, int B, bool split
     return w;
 }
 
+// Tile 8, one pixel per thread: the warp-per-block forward (k_render_fwd_w).
+template <int REC>
+static dg_status launch_fwd_w(const float* feat, const uint32_t* gid, const uint32_t* ranges, const dg::RViews& rv,
+                              const RenderWs& w, int split_req, float* img, float* T, int* last, int* ex, int* bl,
+                              cudaStream_t s)
+{
+    const uint2* rg = (const uint2*)ranges;
+    auto kern = dg::k_render_fwd_w<false, REC>;
+    const int R = resident_ctas(kern, 64);
+    cudaMemsetAsync(w.hdr, 0, 256, s);
+    if (w.flags && w.flags_cap > 0) cudaMemsetAsync(w.flags, 0, (size_t)w.flags_cap, s);
+    const bool split = rv.total > 0 && (split_req > 0 || (split_req == 0 && rv.total < 2LL * R));
+    if (split) {
+        const dg::SplitCfg cfg{split_req, R, w.cap};
+        const long long n = rv.total;
+        const int nb = (int)((n + dg::SCAN_TILE - 1) / dg::SCAN_TILE);
+        dg::k_scan_reduce<<<nb, dg::SCAN_THREADS, 0, s>>>(dg::LoadLen{rg}, n, w.bsum);
+        dg::k_scan_top<<<1, 1024, 0, s>>>(w.bsum, nb, &w.hdr->M);
+        dg_note_launch(2);
+        dg::exclusive_scan(dg::LoadChunks{rg, w.hdr, cfg}, n, w.toff, w.bsum, &w.hdr->totals, s);
+        const int pg = (int)((n + 255) / 256);
+        dg::k_plan_items<<<pg < 1024 ? pg : 1024, 256, 0, s>>>(rg, (int)n, w.hdr, cfg, w.toff, w.items, w.sitems);
+        auto kprod = dg::k_render_fwd_w<true, REC>;
+        kprod<<<resident_ctas(kprod, 64), 64, 0, s>>>((const void*)feat, gid, rg, rv, w.hdr, w.items, w.sitems, w.sl,
+                                                      nullptr, 0, img, T, last, ex, bl);
+        dg_note_launch(2);
+    }
+    const int grid = split ? R : (R < rv.total ? R : (rv.total > 0 ? rv.total : 1));
+    kern<<<grid, 64, 0, s>>>((const void*)feat, gid, rg, rv, w.hdr, w.items, w.sitems, w.sl, w.flags, w.flags_cap,
+                             img, T, last, ex, bl);
+    dg_note_launch();
+    if (split) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        dg::k_render_combine<8><<<4 * (sms > 0 ? sms : 1), 64, 0, s>>>(rg, rv, w.hdr, w.sitems, w.sl, img, T, last,
+                                                                      ex, bl);
+        dg_note_launch();
+    }
+    return DG_OK;
+}
+
 template <int B, int PPT, int REC>
 static dg_status launch_fwd(const float* feat, const uint32_t* gid, const uint32_t* ranges, const dg::RViews& rv,
                             const RenderWs& w, int split_req, float* img, float* T, int* last, int* ex, int* bl,
                             cudaStream_t s)
 {
     const uint2* rg = (const uint2*)ranges;
+    if (B == 8 && PPT == 1) return launch_fwd_w<REC>(feat, gid, ranges, rv, w, split_req, img, T, last, ex, bl, s);
     auto kern = dg::k_render_fwd<B, PPT, false, REC>;
     const int R = resident_ctas(kern, B * B / PPT);
     cudaMemsetAsync(w.hdr, 0, 256, s);
