@@ -141,7 +141,7 @@ struct SrcKV {
 
 // One stable pass on digit (key >> shift) & mask; kout may be null (values only).
 template <class Src>
-__global__ void __launch_bounds__(RS_THREADS)
+__global__ void __launch_bounds__(RS_THREADS, 4)
 k_os_pass(Src src, uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const long long* n_dev,
           long long n_cap, OsPass ps)
 {
@@ -170,20 +170,11 @@ k_os_pass(Src src, uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, con
 #pragma unroll
     for (int k = 0; k < RS_IPT; ++k) {
         const long long i = seg + (long long)k * 32 + lane;
-        const bool ok = i < n;
         key[k] = 0u;
         val[k] = 0u;
-        if (ok) src(i, key[k], val[k]);
-        // out-of-range lanes get a digit no valid lane can have
-        const uint32_t d = ok ? ((key[k] >> ps.shift) & ps.mask) : (0x10000u + (uint32_t)lane);
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t before = 0;
-        if (ok) before = cnt[warp][d];
-        __syncwarp();
-        rank[k] = before + __popc(peers & lt);
-        if (ok && (peers & lt) == 0) cnt[warp][d] = before + __popc(peers);
-        __syncwarp();
+        if (i < n) src(i, key[k], val[k]);
     }
+    warp_rank(key, rank, seg, n, ps.shift, ps.mask, false, cnt[warp], lane, lt);
     __syncthreads();
     // per digit: exclusive prefix over warps (tile-local) and the tile total;
     // the aggregate is published at once so that later tiles can pass it

@@ -5,9 +5,9 @@
 //
 // Radix pass = per-block digit histogram, exclusive scan of the digit-major
 // histogram, stable scatter.  Each warp owns a contiguous segment of a block's
-// tile and ranks equal digits with __match_any_sync; per-warp digit counts
-// give the block-local offsets, so the scatter is stable without a block-wide
-// sort.
+// tile and finds the lanes with equal digits by one ballot per digit bit;
+// per-warp digit counts give the block-local offsets, so the scatter is
+// stable without a block-wide sort.
 #pragma once
 
 #include "common.cuh"
@@ -24,6 +24,61 @@ constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_IPT = 8;
 constexpr int RS_TILE = RS_THREADS * RS_IPT;
 constexpr int RS_MAXBITS = 8;
+
+// Lanes of the warp holding the same `nbits`-bit digit as this lane, among the
+// lanes with ok set (the mask __match_any_sync would give over those lanes),
+// from one ballot per digit bit: the cost does not grow with the number of
+// distinct digits in the warp.  A lane without ok gets its own bit only.
+__device__ __forceinline__ uint32_t warp_peers(uint32_t d, int nbits, bool ok, int lane)
+{
+    uint32_t m = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+    for (int b = 0; b < RS_MAXBITS; ++b) {
+        if (b < nbits) {
+            const bool bit = (d >> b) & 1u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+            m &= bit ? bal : ~bal;
+        }
+    }
+    return ok ? m : (1u << lane);
+}
+
+// Stable rank of a warp's RS_IPT x 32 keys (item k of lane l at position
+// seg + 32 k + l, valid below n) among the equal digits of the warp's
+// segment, in position order; wcnt: the warp's running count of each digit
+// (zero on entry, the digit totals on return).  Peer masks by ballots
+// (`ballot`: fixed cost, for digits that are nearly all distinct within a
+// warp) or by __match_any_sync (fast when a warp holds few distinct digits).
+__device__ __forceinline__ void warp_rank(const uint32_t (&key)[RS_IPT], uint32_t (&rank)[RS_IPT], long long seg,
+                                          long long n, int shift, uint32_t mask, bool ballot, uint32_t* wcnt,
+                                          int lane, uint32_t lt)
+{
+    const int nbits = __popc(mask);
+    uint32_t peers[RS_IPT];
+    if (ballot) {
+#pragma unroll
+        for (int k = 0; k < RS_IPT; ++k)
+            peers[k] = warp_peers((key[k] >> shift) & mask, nbits, seg + (long long)k * 32 + lane < n, lane);
+    } else {
+#pragma unroll
+        for (int k = 0; k < RS_IPT; ++k) {
+            // out-of-range lanes get a digit no valid lane can have
+            const bool ok = seg + (long long)k * 32 + lane < n;
+            peers[k] = __match_any_sync(0xffffffffu, ok ? ((key[k] >> shift) & mask) : (0x10000u + (uint32_t)lane));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < RS_IPT; ++k) {
+        const bool ok = seg + (long long)k * 32 + lane < n;
+        const uint32_t d = (key[k] >> shift) & mask;
+        uint32_t before = 0;
+        if (ok) before = wcnt[d];
+        __syncwarp();
+        rank[k] = before + __popc(peers[k] & lt);
+        if (ok && (peers[k] & lt) == 0) wcnt[d] = before + __popc(peers[k]);
+        __syncwarp();
+    }
+}
 
 template <typename T>
 __device__ inline T warp_incl_scan(T x, int lane)
@@ -167,14 +222,14 @@ k_rs_hist(const uint32_t* __restrict__ keys, const long long* n_dev, long long n
 }
 
 // Stable scatter of one radix pass.  Ranks are computed per warp-owned
-// segment (match_any within each 32-item round, running per-warp digit
+// segment (ballot peer masks within each 32-item round, running per-warp digit
 // counts), the block's items are first placed in shared memory in digit order,
 // then written out so that consecutive threads write consecutive addresses of
 // each digit's run.  kout may be null (values only).
-__global__ void __launch_bounds__(RS_THREADS)
+__global__ void __launch_bounds__(RS_THREADS, 4)
 k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const long long* n_dev,
-             long long n_cap, int shift, uint32_t mask, const uint32_t* __restrict__ offs, int nblk)
+             long long n_cap, int shift, uint32_t mask, bool ballot, const uint32_t* __restrict__ offs, int nblk)
 {
     __shared__ uint32_t cnt[RS_WARPS][1 << RS_MAXBITS];
     __shared__ uint32_t dstart[1 << RS_MAXBITS];
@@ -192,22 +247,14 @@ k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
     __syncwarp();
     uint32_t key[RS_IPT], val[RS_IPT], rank[RS_IPT];
     const uint32_t lt = (1u << lane) - 1u;
+    // all loads first, then the peer masks, then the running per-warp counts
 #pragma unroll
     for (int k = 0; k < RS_IPT; ++k) {
         const long long i = seg + (long long)k * 32 + lane;
-        const bool ok = i < n;
-        key[k] = ok ? kin[i] : 0u;
-        val[k] = ok ? vin[i] : 0u;
-        // out-of-range lanes get a digit no valid lane can have
-        const uint32_t d = ok ? ((key[k] >> shift) & mask) : (0x10000u + (uint32_t)lane);
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t before = 0;
-        if (ok) before = cnt[warp][d];
-        __syncwarp();
-        rank[k] = before + __popc(peers & lt);
-        if (ok && (peers & lt) == 0) cnt[warp][d] = before + __popc(peers);
-        __syncwarp();
+        key[k] = i < n ? kin[i] : 0u;
+        val[k] = i < n ? vin[i] : 0u;
     }
+    warp_rank(key, rank, seg, n, shift, mask, ballot, cnt[warp], lane, lt);
     __syncthreads();
     // per digit: exclusive prefix over warps (block-local), digit total, global start
     uint32_t total = 0;
@@ -261,7 +308,7 @@ struct KV { uint32_t* k; uint32_t* v; };
 
 static KV radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* kfin,
                      uint32_t* vfin, const long long* n_dev, long long n_cap, int bits,
-                     const SortBufs& sb, cudaStream_t s, bool hist0_ready = false)
+                     const SortBufs& sb, cudaStream_t s, bool hist0_ready = false, uint32_t ballot_passes = 0)
 {
     const int nblk = (int)((n_cap + RS_TILE - 1) / RS_TILE);
     if (nblk == 0) return KV{k0, v0};
@@ -286,7 +333,8 @@ static KV radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uin
         }
         const long long nh = (long long)(mask + 1) * nblk;
         exclusive_scan(LoadU32{sb.hist}, nh, sb.hist, sb.bsum, (long long*)nullptr, s);
-        k_rs_scatter<<<nblk, RS_THREADS, 0, s>>>(ks, vs, kd, vd, n_dev, n_cap, shift, mask, sb.hist, nblk);
+        k_rs_scatter<<<nblk, RS_THREADS, 0, s>>>(ks, vs, kd, vd, n_dev, n_cap, shift, mask, (ballot_passes >> p) & 1u,
+                                                 sb.hist, nblk);
         dg_note_launch();
         ks = kd;
         vs = vd;
