@@ -97,7 +97,16 @@ typedef struct dg_camera {
  * variant of the supplementary): the 2D covariance gets + mip2d I instead of
  * + eps2d I and the opacity of the record is scaled by
  * sqrt(det(S2) / det(S2 + mip2d I)) (0 when det(S2) <= 0); dg_project_bwd
- * differentiates the factor. */
+ * differentiates the factor.
+ * tight_bins: 0 = each Gaussian's pair list covers every tile of its rect
+ * (Sec. 2's tile binning as written); 1 = dg_project leaves out the tiles of
+ * a rect of at most 8 x 8 tiles where no pixel centre inside the image can
+ * give the Gaussian an alpha >= 1/255 (a closed-form bound of its quadratic
+ * form over the tile, with a margin for float32 rounding, checked for the
+ * float32 record and for its float16 conic and opacity).  Such an entry is
+ * skipped by every pixel of that tile in both compositing passes, so images,
+ * transmittances and gradients are the same; the lists are shorter (list
+ * positions in `last` count the entries of the shorter lists). */
 typedef struct dg_raster_opts {
     int32_t tile;
     int32_t sh_degree;
@@ -108,6 +117,7 @@ typedef struct dg_raster_opts {
     int32_t split_len;
     int32_t record;
     float mip2d;
+    int32_t tight_bins;
 } dg_raster_opts;
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
@@ -138,12 +148,17 @@ DG_API int64_t dg_kernel_launches(void);
  * In:  params [59][stride] planar float32, P Gaussians, cams[n_views], *opts (host).
  * Out (per record r = v * P + i):
  *      feat   [P][12] float32, 16-byte aligned, per record
- *              (u, v, A, B | C, o, r, g | b, 0, 0, 0): pixel mean, conic
+ *              (u, v, A, B | C, o, r, g | b, m0, m1, 0): pixel mean, conic
  *              (A, B, C) = inverse 2D covariance (power = -A dx^2/2 - C dy^2/2
- *              - B dx dy), opacity, colour;
+ *              - B dx dy), opacity, colour; m0, m1 (uint32 bits): with
+ *              opts->tight_bins, the low and high words of the 64-bit mask of
+ *              the rect's tiles kept in the pair list (bit 8 ry + rx for tile
+ *              (x0 + rx, y0 + ry)), 0 for "every tile of the rect" (always
+ *              without tight_bins, and for rects wider or taller than 8 tiles);
  *      depth  [P] camera-space z;
  *      radius [P] int32, 0 when culled (near plane, singular, empty rect);
- *      tiles  [P] int32, number of tiles in the rect (0 when culled);
+ *      tiles  [P] int32, number of pair-list tiles: the tiles in the rect, or
+ *              the kept tiles of the mask (0 when culled);
  *      clamp  [P] uint8, bit c set when colour channel c was clamped at 0.
  * Errors: DG_ERR_ARG for null pointers, P < 0, stride < P, sh_degree
  * outside 0..3, tile < 1, non-positive image size or focal length. */
@@ -154,7 +169,8 @@ DG_API dg_status dg_project(const float* params, int64_t stride, int64_t P, cons
 /* ---------------------------------------------------------------------- */
 /* Tile binning and ordering (the tile-based "GPU-friendly rendering
  * pipeline" of Sec. 2 that evaluates Eq. 1 front to back).  The pair list of
- * a view holds one (tile, Gaussian) entry per tile in each Gaussian's rect,
+ * a view holds one (tile, Gaussian) entry per tile in each Gaussian's rect
+ * (per kept tile with opts->tight_bins),
  * ordered by (tile id = ty * TX + tx, depth as float bits, Gaussian index).
  *
  * Bytes of device workspace needed to bin P Gaussians in n_views views into
@@ -172,7 +188,8 @@ DG_API dg_status dg_bin_count(const float* depth, const int32_t* tiles, int64_t 
                        size_t ws_bytes, int64_t M_cap, int64_t* M_out, dg_stream stream);
 
 /* Phase 2: emits the pairs in (view, depth) order and stably sorts them by
- * global tile id.
+ * global tile id.  A record whose feat holds a tile mask (opts->tight_bins
+ * of dg_project) gets pairs only for the mask's tiles.
  * Out: gid    [M_cap] uint32, record index v * P + i of each sorted pair;
  *      ranges [2 * total tiles] uint32, [start, end) of each tile's list;
  *      status (device int32): 0, or DG_ERR_CAPACITY when M > M_cap, in which

@@ -51,7 +51,8 @@ class Camera(ctypes.Structure):
 class RasterOpts(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("near_plane", ctypes.c_float),
                 ("eps2d", ctypes.c_float), ("bg", ctypes.c_float * 3), ("pixels_per_thread", ctypes.c_int32),
-                ("split_len", ctypes.c_int32), ("record", ctypes.c_int32), ("mip2d", ctypes.c_float)]
+                ("split_len", ctypes.c_int32), ("record", ctypes.c_int32), ("mip2d", ctypes.c_float),
+                ("tight_bins", ctypes.c_int32)]
 
 
 SCHED_MAX_LEVELS = 64
@@ -102,7 +103,7 @@ def camera(viewmat, fx, fy, cx, cy, width, height) -> Camera:
 
 
 def raster_opts(tile=16, sh_degree=3, near_plane=0.2, eps2d=0.3, bg=(0.0, 0.0, 0.0),
-                pixels_per_thread=0, split_len=0, record=0, mip2d=0.0) -> RasterOpts:
+                pixels_per_thread=0, split_len=0, record=0, mip2d=0.0, tight_bins=0) -> RasterOpts:
     o = RasterOpts()
     o.tile, o.sh_degree, o.near_plane, o.eps2d = int(tile), int(sh_degree), float(near_plane), float(eps2d)
     o.bg[:] = [float(b) for b in bg]
@@ -110,6 +111,7 @@ def raster_opts(tile=16, sh_degree=3, near_plane=0.2, eps2d=0.3, bg=(0.0, 0.0, 0
     o.split_len = int(split_len)
     o.record = int(record)
     o.mip2d = float(mip2d)
+    o.tight_bins = int(tight_bins)
     return o
 
 

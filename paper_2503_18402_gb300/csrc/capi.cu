@@ -34,4 +34,4 @@ dg_status dg_check_launch(const char* what)
 
 extern "C" const char* dg_last_error(void) { return g_err; }
 
-extern "C" int32_t dg_abi_version(void) { return 6; }
+extern "C" int32_t dg_abi_version(void) { return 7; }

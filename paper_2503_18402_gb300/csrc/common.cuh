@@ -96,6 +96,48 @@ __device__ __forceinline__ void adam_update(float& p, float& m, float& v, float 
     p -= __fdividef(r.step * m, fmaf(sv, r.inv_bc2, h.eps));
 }
 
+// Smallest value of A dx^2 + 2 B dx dy + C dy^2 over dx in [dxl, dxh], dy in [dyl, dyh]
+// (positive-definite form; 0 when the box contains the origin), less a bound
+// on its float32 rounding (a multiple of the magnitude of the summed terms).
+__device__ inline float quad_min_box(float A, float B, float C, float dxl, float dxh, float dyl, float dyh)
+{
+    if (dxl <= 0.f && dxh >= 0.f && dyl <= 0.f && dyh >= 0.f) return 0.f;
+    float best = 3.4e38f;
+    // edges dx = const: minimiser dy* = -B dx / C, clamped; then dy = const
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float dx, dy;
+        // (the minimiser only has to be near the edge's minimum: the form is
+        // flat there, so the fast division changes f by a second-order amount)
+        if (e < 2) {
+            dx = e ? dxh : dxl;
+            dy = fminf(fmaxf(__fdividef(-B * dx, C), dyl), dyh);
+        } else {
+            dy = (e & 1) ? dyh : dyl;
+            dx = fminf(fmaxf(__fdividef(-B * dy, A), dxl), dxh);
+        }
+        const float f = A * dx * dx + 2.f * B * dx * dy + C * dy * dy;
+        const float mag = A * dx * dx + 2.f * fabsf(B * dx * dy) + C * dy * dy;
+        best = fminf(best, f - 1e-5f * mag);
+    }
+    return best;
+}
+
+// True when no pixel centre of the rectangle [px0, px1] x [py0, py1] can give
+// the Gaussian of record (a, b) = (u, v, A, B | C, o, ...) an alpha >= 1/255.
+// The render passes drop such entries per tile or pixel block when they stage
+// a batch; the projection uses it to leave tiles out of the pair list
+// (tight_bins).
+__device__ inline bool tile_skip(const float4& a, const float4& b, float px0, float px1, float py0, float py1)
+{
+    const float o = b.y;
+    if (!(o >= kAlphaMin)) return true;  // alpha <= o < 1/255 everywhere
+    const float fmin = quad_min_box(a.z, a.w, b.x, a.x - px1, a.x - px0, a.y - py1, a.y - py0);
+    // alpha = o exp(-fmin/2) < 1/255  <=>  fmin > 2 ln(255 o); 0.02 absorbs the
+    // per-pixel rounding of the power and of exp
+    return fmin > 2.f * __logf(255.f * o) + 0.02f;
+}
+
 }  // namespace dg
 
 // Host-side error reporting shared by the C-ABI entry points.

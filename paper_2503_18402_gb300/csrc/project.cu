@@ -17,6 +17,8 @@
 // Adjoint: per view, the 2D gradients are pulled back to dL/dt, dL/dSigma and
 // the colour terms; dL/dSigma is summed over the views and pushed through
 // Sigma = M M^T, M = Rq S and the quaternion normalisation once.
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace dg {
@@ -214,13 +216,67 @@ __device__ inline const ViewSet& block_views(const ViewSet& vs, const dg_camera*
 // Resident 128-thread CTAs per SM requested from the compiler (a register
 // bound: 5 gives 96 registers; measured 0.132 -> 0.128 ms at 2M Gaussians,
 // 6 no better).
+// x as a float16 holds it (round to nearest): the conic and opacity of the
+// mixed-precision records.
+__device__ inline float round_f16(float x) { return __half2float(__float2half_rn(x)); }
+
+// Tiles of the rect q where a record with pixel mean (u, v), conic (A, B, C)
+// and opacity o may blend: bit 8 ry + rx for the tile (q.x0 + rx, q.y0 + ry).
+// A pixel centre d from the mean blends only when f = A dx^2 + 2 B dx dy +
+// C dy^2 <= 2 ln(255 o).  That ellipse meets the band of a tile row's pixel
+// centres in one x-interval: its ends lie where the ellipse's rightmost
+// (leftmost) point, clamped to the band, sits, with the half-width
+// sqrt(det(S)/Syy (t - dy^2/Syy)) around the centre line dx = (Sxy/Syy) dy of
+// the covariance S = conic^-1 (the 2x2 determinant in Kahan's fma form).  The
+// threshold and the interval are widened (1e-3 relative, 0.02 absolute on f;
+// 0.01 px and 1e-3 relative on x) beyond the float32 rounding of the render's
+// per-pixel test: a radius of at most 4 tiles bounds the Gaussian's extent
+// and so the conditioning of f (at most 3e-4 relative error there).  False
+// (no mask) when the rect is wider or taller than 8 tiles or the radius r
+// exceeds 4 tiles (a large Gaussian whose rect was clipped by the image).
+__device__ inline bool tile_mask(float u, float v, float A, float B, float C, float o, int r, const Rect& q, int Bt,
+                                 uint64_t* mask)
+{
+    if (q.x1 - q.x0 > 8 || q.y1 - q.y0 > 8 || r > 4 * Bt) return false;
+    uint64_t m = 0;
+    if (o >= kAlphaMin) {
+        const float t = fmaf(2.f * logf(255.f * o), 1.001f, 0.02f);
+        const float bb = B * B;
+        const float det = fmaf(A, C, -bb) - fmaf(B, B, -bb);  // A C - B^2
+        const float id = 1.f / det;                            // det(S)
+        const float sa = C * id, sb = -B * id, sc = A * id;    // S = [[sa, sb], [sb, sc]]
+        const float isc = 1.f / sc;
+        const float ky = sb * isc;                             // centre line dx = ky dy
+        const float w2 = id * isc;                             // det(S) / Syy
+        const float ry = fmaf(sqrtf(t * sc), 1.001f, 0.01f);   // dy half-extent of the ellipse
+        const float dyr = sb * sqrtf(t / sa);                  // dy of the rightmost point
+        const float fb = (float)Bt;
+        for (int ty = q.y0; ty < q.y1; ++ty) {
+            const float yl = fmaf((float)ty, fb, 0.5f) - v;
+            const float lo = fmaxf(yl, -ry), hi = fminf(yl + (fb - 1.f), ry);
+            if (lo > hi) continue;
+            const float d1 = fminf(fmaxf(dyr, lo), hi), d2 = fminf(fmaxf(-dyr, lo), hi);
+            const float xr = fmaf(ky, d1, sqrtf(fmaxf(0.f, w2 * fmaf(-d1 * d1, isc, t))));
+            const float xl = fmaf(ky, d2, -sqrtf(fmaxf(0.f, w2 * fmaf(-d2 * d2, isc, t))));
+            const float eta = fmaf(1e-3f, fabsf(xl) + fabsf(xr), 0.01f);
+            // tiles whose pixel-centre columns [tx B + 0.5, tx B + B - 0.5] meet [u + xl, u + xr]
+            const int ta = max(q.x0, (int)ceilf((u + xl - eta - (fb - 0.5f)) / fb));
+            const int tb = min(q.x1 - 1, (int)floorf((u + xr + eta - 0.5f) / fb));
+            if (ta > tb) continue;
+            m |= ((2ull << (tb - ta)) - 1ull) << (8 * (ty - q.y0) + (ta - q.x0));
+        }
+    }
+    *mask = m;
+    return true;
+}
+
 #ifndef DG_PROJECT_FWD_MINB
 #define DG_PROJECT_FWD_MINB 5
 #endif
 template <int NB>
 __global__ void __launch_bounds__(128, DG_PROJECT_FWD_MINB)
 k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs_host, const dg_camera* cdev, int B,
-              float near_plane, float eps2d, float mip2d, float4* __restrict__ feat, float* __restrict__ depth,
+              float near_plane, float eps2d, float mip2d, int tight, float4* __restrict__ feat, float* __restrict__ depth,
               int* __restrict__ radius, int* __restrict__ tiles, uint8_t* __restrict__ clampm)
 {
     __shared__ ViewSet s_vs;
@@ -273,6 +329,14 @@ k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs
                     f0 = make_float4(u, vv, S.A, S.B);
                     f1 = make_float4(S.C, osig * S.comp, col[0], col[1]);
                     f2 = make_float4(col[2], 0.f, 0.f, 0.f);
+                    uint64_t m;
+                    const bool r16 = tight > 1;  // the render reads float16 conic and opacity
+                    if (tight && tile_mask(u, vv, r16 ? round_f16(S.A) : S.A, r16 ? round_f16(S.B) : S.B,
+                                           r16 ? round_f16(S.C) : S.C, r16 ? round_f16(f1.y) : f1.y, rr, q, B, &m)) {
+                        nt = __popcll(m);  // 0: no tile of the rect can blend the record
+                        f2.y = __uint_as_float((uint32_t)m);
+                        f2.z = __uint_as_float((uint32_t)(m >> 32));
+                    }
                 }
             }
         }
@@ -576,10 +640,10 @@ extern "C" dg_status dg_project(const float* params, int64_t stride, int64_t P, 
     const int blocks = (int)((P + threads - 1) / threads);
     cudaStream_t s = (cudaStream_t)stream;
     switch (opts->sh_degree) {
-    case 0: dg::k_project_fwd<1><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, opts->mip2d, (float4*)feat, depth, radius, tiles, clamp); break;
-    case 1: dg::k_project_fwd<4><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, opts->mip2d, (float4*)feat, depth, radius, tiles, clamp); break;
-    case 2: dg::k_project_fwd<9><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, opts->mip2d, (float4*)feat, depth, radius, tiles, clamp); break;
-    default: dg::k_project_fwd<16><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, opts->mip2d, (float4*)feat, depth, radius, tiles, clamp); break;
+    case 0: dg::k_project_fwd<1><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, opts->mip2d, opts->tight_bins ? 1 + (opts->record == 1) : 0, (float4*)feat, depth, radius, tiles, clamp); break;
+    case 1: dg::k_project_fwd<4><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, opts->mip2d, opts->tight_bins ? 1 + (opts->record == 1) : 0, (float4*)feat, depth, radius, tiles, clamp); break;
+    case 2: dg::k_project_fwd<9><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, opts->mip2d, opts->tight_bins ? 1 + (opts->record == 1) : 0, (float4*)feat, depth, radius, tiles, clamp); break;
+    default: dg::k_project_fwd<16><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, opts->mip2d, opts->tight_bins ? 1 + (opts->record == 1) : 0, (float4*)feat, depth, radius, tiles, clamp); break;
     }
     dg_note_launch();
     return dg_check_launch("project_fwd");

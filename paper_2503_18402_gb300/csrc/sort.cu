@@ -126,10 +126,15 @@ k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const ui
        int* status)
 {
     const uint32_t n_tiles = (uint32_t)tg.off[tg.n];
-    __shared__ int w_start[RS_TILE];      // pair offset of each staged Gaussian, relative to the block
+    // staged Gaussians: pair offset relative to the block (the first one's,
+    // <= 0, in s_first; the others' lie in 1 .. RS_TILE - 1), rect corner,
+    // rect width and view, record index, tile mask (0: every tile of the rect)
+    __shared__ uint16_t w_start[RS_TILE];
     __shared__ uint32_t w_xy[RS_TILE];    // rect x0 | y0 << 16
     __shared__ uint32_t w_wv[RS_TILE];    // rect width in tiles | view << 16
     __shared__ uint32_t w_g[RS_TILE];     // record index
+    __shared__ unsigned long long w_m[RS_TILE];
+    __shared__ int s_first;
     __shared__ int s_off[DG_MAX_VIEWS];   // global tile id of each view's tile (0, 0)
     __shared__ int s_tx[DG_MAX_VIEWS];    // tiles per row of each view
     __shared__ uint32_t h[1 << RS_MAXBITS];
@@ -183,11 +188,15 @@ k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const ui
                 const uint32_t g = gk[k];
                 const int v = (int)(g / Pv);
                 const float4 f0 = feat[3 * (size_t)g];
+                const float4 f2 = feat[3 * (size_t)g + 2];
                 const Rect q = tile_rect(f0.x, f0.y, radius[g], B, tg.TX[v], tg.TY[v]);
-                w_start[w] = (int)(st[k] - base);
+                if (w == 0) s_first = (int)(st[k] - base);
+                else w_start[w] = (uint16_t)(st[k] - base);
                 w_xy[w] = (uint32_t)q.x0 | ((uint32_t)q.y0 << 16);
                 w_wv[w] = (uint32_t)(q.x1 - q.x0) | ((uint32_t)v << 16);
                 w_g[w] = g;
+                w_m[w] = (unsigned long long)__float_as_uint(f2.y) |
+                         ((unsigned long long)__float_as_uint(f2.z) << 32);
                 top = w + 1;
             }
         }
@@ -199,19 +208,28 @@ k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const ui
         const int rel0 = (int)threadIdx.x * RS_IPT;
         const int nblock = (int)(end - base);
         if (rel0 < nblock) {
-            int lo = 0, hi = nw - 1;  // w_start[0] <= 0 <= rel0
+            int lo = 0, hi = nw - 1;  // the first staged Gaussian starts at or before 0 <= rel0
             while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (w_start[mid] <= rel0) lo = mid; else hi = mid - 1;
+                const int mid = (lo + hi + 1) >> 1;  // >= 1
+                if ((int)w_start[mid] <= rel0) lo = mid; else hi = mid - 1;
             }
-            int j = rel0 - w_start[lo];
+            const int j = rel0 - (lo > 0 ? (int)w_start[lo] : s_first);
             uint32_t wv = w_wv[lo];
             int wx = (int)(wv & 0xffffu);
             uint32_t xy = w_xy[lo];
             uint32_t g = w_g[lo];
+            // with a tile mask, pair j is the j-th set bit (row-major, 8 bits per row)
+            unsigned long long mk = w_m[lo];
             int tb = s_off[wv >> 16], TXv = s_tx[wv >> 16];
-            int next = lo + 1 < nw ? w_start[lo + 1] : nblock;
-            int ry = j / wx, rx = j - ry * wx;
+            int next = lo + 1 < nw ? (int)w_start[lo + 1] : nblock;
+            int rx, ry;
+            if (mk) {
+                for (int c = 0; c < j; ++c) mk &= mk - 1;
+                const int b = __ffsll((long long)mk) - 1;
+                rx = b & 7; ry = b >> 3;
+            } else {
+                ry = j / wx; rx = j - ry * wx;
+            }
             uint32_t kk[RS_IPT], vv[RS_IPT];
             const int cnt = nblock - rel0 < RS_IPT ? nblock - rel0 : RS_IPT;
 #pragma unroll
@@ -221,9 +239,15 @@ k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const ui
                         ++lo;
                         wv = w_wv[lo];
                         wx = (int)(wv & 0xffffu); xy = w_xy[lo]; g = w_g[lo];
+                        mk = w_m[lo];
                         tb = s_off[wv >> 16]; TXv = s_tx[wv >> 16];
-                        next = lo + 1 < nw ? w_start[lo + 1] : nblock;
-                        rx = 0; ry = 0;
+                        next = lo + 1 < nw ? (int)w_start[lo + 1] : nblock;
+                        if (mk) {
+                            const int b = __ffsll((long long)mk) - 1;
+                            rx = b & 7; ry = b >> 3;
+                        } else {
+                            rx = 0; ry = 0;
+                        }
                     }
                     uint32_t key = (uint32_t)(tb + ((int)(xy >> 16) + ry) * TXv + (int)(xy & 0xffffu) + rx);
                     if (key >= n_tiles) {  // cannot happen for consistent inputs; never index past the grid
@@ -233,7 +257,13 @@ k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const ui
                     kk[e] = key;
                     vv[e] = g;
                     atomicAdd(&h[key & mask0], 1u);
-                    if (++rx == wx) { rx = 0; ++ry; }
+                    if (mk) {
+                        mk &= mk - 1;  // the next kept tile (none left when the Gaussian's pairs end)
+                        const int b = __ffsll((long long)mk) - 1;
+                        rx = b & 7; ry = b >> 3;
+                    } else if (++rx == wx) {
+                        rx = 0; ++ry;
+                    }
                 }
             }
             const long long i0 = base + rel0;

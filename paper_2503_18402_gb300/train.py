@@ -101,6 +101,9 @@ class TrainConfig:
     fused_adam: bool = True
     # V > 1: Adam learning rates x sqrt(V) and betas ^ V (Grendel-GS batch rules)
     batch_adam_scaling: bool = True
+    # pair lists hold only the tiles where a Gaussian can reach alpha 1/255
+    # (same images and gradients, shorter lists to sort and stage)
+    tight_bins: bool = True
     seed: int = 0
 
 
@@ -125,7 +128,7 @@ class Trainer:
         self.acc = torch.zeros(cap, **f32)
         self.den = torch.zeros(cap, **f32)
         self.maxr = torch.zeros(cap, **f32)
-        self.tuner = RenderTuner(self.dev, capi.raster_opts(record=cfg.record, mip2d=cfg.mip2d),
+        self.tuner = RenderTuner(self.dev, capi.raster_opts(record=cfg.record, mip2d=cfg.mip2d, tight_bins=int(cfg.tight_bins)),
                                  fixed=None if cfg.autotune else Shape(16, 2, 4, 0))
         self.rz = self.tuner.rasterizer(Shape(8, 1, 1, 0))  # evaluation renders
         n_full = 3 * self.H * self.W
@@ -278,7 +281,8 @@ class Trainer:
                 fr0 = rz0.forward(b["p"][:, :P], P, cams, self.stream)
                 hint = fr0.M
             M_cap = int(hint * 1.5) + 4096
-            g = StepGraph(self.dev, capi.raster_opts(tile=8, record=cfg.record, mip2d=cfg.mip2d), 1, 1, b["p"],
+            g = StepGraph(self.dev, capi.raster_opts(tile=8, record=cfg.record, mip2d=cfg.mip2d,
+                                                   tight_bins=int(cfg.tight_bins)), 1, 1, b["p"],
                           b["m"], b["v"],
                           self.grads, self.cap, P,
                           cams, M_cap, cfg.ssim_lambda, (self.acc, self.den, self.maxr) if stats_on else None,

@@ -51,7 +51,7 @@ def test_binding_covers_every_export():
 
 def test_host_only_calls_without_gpu():
     from paper_2503_18402_gb300 import capi
-    assert capi.dg_abi_version() == 6
+    assert capi.dg_abi_version() == 7
     assert capi.dg_bin_workspace_size(1000, 1, 5000) > 5000 * 16
     assert capi.dg_bin_workspace_size(1000, 4, 5000) > capi.dg_bin_workspace_size(1000, 1, 5000)
     assert capi.dg_bin_workspace_size(-1, 1, 0) == 0
