@@ -100,13 +100,14 @@ typedef struct dg_camera {
  * differentiates the factor.
  * tight_bins: 0 = each Gaussian's pair list covers every tile of its rect
  * (Sec. 2's tile binning as written); 1 = dg_project leaves out the tiles of
- * a rect of at most 8 x 8 tiles where no pixel centre inside the image can
- * give the Gaussian an alpha >= 1/255 (a closed-form bound of its quadratic
- * form over the tile, with a margin for float32 rounding, checked for the
- * float32 record and for its float16 conic and opacity).  Such an entry is
- * skipped by every pixel of that tile in both compositing passes, so images,
- * transmittances and gradients are the same; the lists are shorter (list
- * positions in `last` count the entries of the shorter lists). */
+ * a rect of at most 8 x 8 tiles (radius at most 4 tiles) whose pixel centres
+ * all lie outside the ellipse where the Gaussian's alpha reaches 1/255 (the
+ * ellipse's x-interval on each tile row, in closed form, widened beyond
+ * float32 rounding), for the record format opts->record names (render with
+ * the same format).  Such an entry is skipped by every pixel of that tile in
+ * both compositing passes, so images, transmittances and gradients are the
+ * same; the lists are shorter (list positions in `last` count the entries of
+ * the shorter lists). */
 typedef struct dg_raster_opts {
     int32_t tile;
     int32_t sh_degree;

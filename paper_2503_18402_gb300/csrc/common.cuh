@@ -126,8 +126,7 @@ __device__ inline float quad_min_box(float A, float B, float C, float dxl, float
 // True when no pixel centre of the rectangle [px0, px1] x [py0, py1] can give
 // the Gaussian of record (a, b) = (u, v, A, B | C, o, ...) an alpha >= 1/255.
 // The render passes drop such entries per tile or pixel block when they stage
-// a batch; the projection uses it to leave tiles out of the pair list
-// (tight_bins).
+// a batch.
 __device__ inline bool tile_skip(const float4& a, const float4& b, float px0, float px1, float py0, float py1)
 {
     const float o = b.y;
