@@ -116,7 +116,8 @@ class Trainer:
         self.views = train_views
         self.imgs = train_imgs
         self.H, self.W = train_imgs[0].shape[1], train_imgs[0].shape[2]
-        cap = max(cfg.P_cap, init.shape[0]) + 1024
+        # row stride a multiple of 4 floats: 16-byte row accesses in the Adam sweeps
+        cap = (max(cfg.P_cap, init.shape[0]) + 1024 + 3) // 4 * 4
         self.cap = cap
         f32 = dict(dtype=torch.float32, device=self.dev)
         self.buf = [dict(p=torch.zeros((59, cap), **f32), m=torch.zeros((59, cap), **f32),

@@ -498,15 +498,18 @@ def test_adam_parity():
     np.testing.assert_array_equal(got[:, P:], p[:, P:])  # padding untouched
 
 
-@pytest.mark.parametrize("sh,V", [(3, 1), (2, 1), (0, 1), (3, 3), (1, 2)])
-def test_fused_project_bwd_adam_matches_two_calls(sh, V):
+@pytest.mark.parametrize("sh,V,trim,pad", [(3, 1, 0, 13), (2, 1, 0, 13), (0, 1, 0, 13), (3, 3, 0, 13), (1, 2, 0, 13),
+                                          (3, 1, 0, 0), (3, 1, 2, 2), (1, 2, 3, 7)])
+def test_fused_project_bwd_adam_matches_two_calls(sh, V, trim, pad):
     """dg_project_bwd_adam = dg_project_bwd followed by dg_adam_step
     (including Gaussians culled in every view, whose moments still decay).
     The adjoint's two instantiations may contract multiply-adds differently,
     so their gradients agree within the gradient tolerance; the Adam update is
     one contraction-free function, so given the same gradient the state is
-    bit-identical."""
-    g = synth.random_gaussians(3000, 21 + V)
+    bit-identical.  Row strides P + pad: a multiple of 4 (16-byte row accesses
+    in the fused sweep, with P - trim leaving lanes at the end of P) or not
+    (4-byte accesses); columns from P on stay untouched."""
+    g = synth.random_gaussians(3000, 21 + V)[: 3000 - trim]
     g[:, 3:6] += 0.3
     g[-50:, 0] = 100.0  # off-screen in every view: culled, zero gradient, moments still decay
     sizes = [(64, 64), (90, 50), (40, 70)][:V]
@@ -514,7 +517,7 @@ def test_fused_project_bwd_adam_matches_two_calls(sh, V):
     opts = capi.raster_opts(sh_degree=sh)
     rz = Rasterizer("cuda", opts)
     P = g.shape[0]
-    stride = P + 13
+    stride = P + pad
     base = np.zeros((59, stride), np.float32)
     base[:, :P] = g.T
     params = torch.from_numpy(base).cuda()
