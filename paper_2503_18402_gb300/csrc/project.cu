@@ -350,6 +350,41 @@ k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs
     }
 }
 
+// Loads the parameters of the Gaussians c0 .. c0 + 31 (rows 0..58 of the planar
+// [59][stride] array) into columns 32 w .. 32 w + 31 of the shared tile t: 8
+// lanes per row and 16 bytes per lane when `vec` (16-byte aligned rows), all 15
+// loads of a lane issued before its first shared store; 4-byte loads at the end
+// of P.  Columns from P on are left as zeros.
+__device__ inline void stage_params(const float* __restrict__ prm, long long stride, long long c0, long long P,
+                                    bool vec, float (*t)[128], int w, int lane)
+{
+    const int rr = lane >> 3, cc = 4 * (lane & 7);
+    const long long c = c0 + cc;
+    float4 x[15];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+        const int r = 4 * k + rr;
+        x[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < DG_NPARAM) {
+            const float* a = prm + (long long)r * stride + c;
+            if (vec && c + 3 < P) {
+                x[k] = *(const float4*)a;
+            } else {
+                if (c < P) x[k].x = a[0];
+                if (c + 1 < P) x[k].y = a[1];
+                if (c + 2 < P) x[k].z = a[2];
+                if (c + 3 < P) x[k].w = a[3];
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+        const int r = 4 * k + rr;
+        if (r < DG_NPARAM) *(float4*)&t[r][32 * w + cc] = x[k];
+    }
+    __syncwarp();
+}
+
 // Adjoint of the projection, summed over the views.  Each parameter-row
 // gradient goes to `grads` (when given) and, with ADAM, to shared memory; the
 // CTA then runs the Adam update of its 128 Gaussians row by row, so the fused
@@ -384,14 +419,23 @@ k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host,
         // (published by the barrier before the Adam sweep)
     }
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // ADAM: each warp stages its 32 Gaussians' parameters in the gradient tile
+    // (16-byte loads); a thread reads its own column there and overwrites each
+    // row with the row's gradient after its last read of that row
+    if (ADAM)
+        stage_params(prm, stride, (long long)blockIdx.x * blockDim.x + 32 * (threadIdx.x >> 5), P, vec, s_g,
+                     threadIdx.x >> 5, threadIdx.x & 31);
+    const float* src = ADAM ? &s_g[0][0] : prm;  // the thread's parameters: src[row * sst + si]
+    const long long sst = ADAM ? 128 : stride;
+    const int si = ADAM ? (int)threadIdx.x : i;
     auto put = [&](int row, float gval) {
         if (grads) grads[(long long)row * stride + i] = gval;
         if (ADAM) s_g[row][threadIdx.x] = gval;
     };
     auto adjoint = [&]() {
         G3 g;
-        gauss3d(prm, stride, i, g);
-        const float osig = 1.f / (1.f + expf(-prm[10 * stride + i]));
+        gauss3d(src, sst, si, g);
+        const float osig = 1.f / (1.f + expf(-src[10 * sst + si]));
         float dp[3] = {0.f, 0.f, 0.f};
         float dsg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma (xx xy xz yy yz zz), off-diagonals counted once
         float dop = 0.f;
@@ -428,7 +472,7 @@ k_project_bwd(float* __restrict__ prm, long long stride, int P, ViewSet vs_host,
                 for (int k = 0; k < NB; ++k)
     #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) {
-                        const float cw = dcol[ch] * prm[(11 + 3 * k + ch) * stride + i];
+                        const float cw = dcol[ch] * src[(11 + 3 * k + ch) * sst + si];
                         gd[0] += cw * D[k][0];
                         gd[1] += cw * D[k][1];
                         gd[2] += cw * D[k][2];
