@@ -166,6 +166,8 @@ class Trainer:
         self.pending = []  # replayed steps whose status is still to be read
         self.skipped_steps = 0
         self.graph_captures = 0
+        self.capture_s = 0.0  # host seconds in graph captures (each also runs its step)
+        self.densify_s = 0.0  # host seconds in densification (two host reads of device counts)
 
     # ---------------------------------------------------------------- schedule
     def _sched_params(self):
@@ -289,7 +291,9 @@ class Trainer:
                           cams, M_cap, cfg.ssim_lambda, (self.acc, self.den, self.maxr) if stats_on else None,
                           fused=cfg.fused_adam)
             g.key = key
+            tc = time.perf_counter()
             slot = g.capture(cams, hp, targets)
+            self.capture_s += time.perf_counter() - tc
             self.graphs[key] = g
             self.graph_captures += 1
         else:
@@ -386,6 +390,11 @@ class Trainer:
         return r, fr.M
 
     def densify(self, k):
+        td = time.perf_counter()
+        self._densify(k)
+        self.densify_s += time.perf_counter() - td
+
+    def _densify(self, k):
         cfg = self.cfg
         P = self.P
         b = self.buf[self.cur]
@@ -446,7 +455,8 @@ class Trainer:
                     iters_per_factor={str(k): v for k, v in sorted(res_hist.items())},
                     render_shapes=self.tuner.summary(), views_per_step=self.V, steps=self.n_steps,
                     cuda_graph=cfg.cuda_graph, graph_captures=self.graph_captures,
-                    skipped_steps=self.skipped_steps)
+                    skipped_steps=self.skipped_steps, densify_events=len(self.history),
+                    host_densify_s=round(self.densify_s, 3), host_capture_s=round(self.capture_s, 3))
 
 
 def make_dataset(n_gt, n_views, W, H, device, seed=1001, gt=None):
