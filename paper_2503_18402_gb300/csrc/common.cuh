@@ -45,27 +45,32 @@ __host__ __device__ inline void cam_centre(const Cam& c, float out[3])
     for (int k = 0; k < 3; ++k) out[k] = -fmaf(c.r[k], c.t[0], fmaf(c.r[3 + k], c.t[1], c.r[6 + k] * c.t[2]));
 }
 
-__host__ __device__ inline long long floor_div(long long a, long long b)  // b > 0
-{
-    long long q = a / b;
-    if ((a % b) != 0 && a < 0) --q;
-    return q;
-}
-
 // Tile rect [x0, x1) x [y0, y1) of a footprint centred at (u, v) with integer
-// radius r: floor((u -/+ r)/B) computed exactly as floor_div(floor(u) -/+ r, B).
+// radius r: floor((u -/+ r)/B) computed exactly as the floor of (floor(u) -/+ r) / B,
+// clamped to [0, TX] (x1 after adding 1).  The numerator is clamped to
+// [-1, TX B] first, which changes no clamped result (a negative numerator
+// gives a negative quotient, one from TX B on a quotient from TX on), so the
+// division runs in 32 bits instead of a 64-bit division and remainder.
 struct Rect { int x0, y0, x1, y1; };
+
+__device__ inline int floor_div_clamped(long long a, int B, int hi)  // B > 0; -1 for a < 0
+{
+    if (a < 0) return -1;
+    const long long lim = (long long)hi * B;
+    const long long c = a < lim ? a : lim;
+    return c <= 0x7fffffffLL ? (int)c / B : (int)(c / B);
+}
 
 __device__ inline Rect tile_rect(float u, float v, int r, int B, int TX, int TY)
 {
     const long long fu = (long long)floorf(u), fv = (long long)floorf(v);
-    long long x0 = floor_div(fu - r, B), x1 = floor_div(fu + r, B) + 1;
-    long long y0 = floor_div(fv - r, B), y1 = floor_div(fv + r, B) + 1;
+    const int x0 = floor_div_clamped(fu - r, B, TX), x1 = floor_div_clamped(fu + r, B, TX) + 1;
+    const int y0 = floor_div_clamped(fv - r, B, TY), y1 = floor_div_clamped(fv + r, B, TY) + 1;
     Rect q;
-    q.x0 = (int)(x0 < 0 ? 0 : (x0 > TX ? TX : x0));
-    q.x1 = (int)(x1 < 0 ? 0 : (x1 > TX ? TX : x1));
-    q.y0 = (int)(y0 < 0 ? 0 : (y0 > TY ? TY : y0));
-    q.y1 = (int)(y1 < 0 ? 0 : (y1 > TY ? TY : y1));
+    q.x0 = x0 < 0 ? 0 : (x0 > TX ? TX : x0);
+    q.x1 = x1 < 0 ? 0 : (x1 > TX ? TX : x1);
+    q.y0 = y0 < 0 ? 0 : (y0 > TY ? TY : y0);
+    q.y1 = y1 < 0 ? 0 : (y1 > TY ? TY : y1);
     return q;
 }
 

@@ -216,6 +216,14 @@ __device__ inline const ViewSet& block_views(const ViewSet& vs, const dg_camera*
 // Resident 128-thread CTAs per SM requested from the compiler (a register
 // bound: 5 gives 96 registers; measured 0.132 -> 0.128 ms at 2M Gaussians,
 // 6 no better).
+// Square root on the special-function unit (sqrt.approx: a few ulps).
+__device__ inline float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // x as a float16 holds it (round to nearest): the conic and opacity of the
 // mixed-precision records.
 __device__ inline float round_f16(float x) { return __half2float(__float2half_rn(x)); }
@@ -240,28 +248,30 @@ __device__ inline bool tile_mask(float u, float v, float A, float B, float C, fl
     if (q.x1 - q.x0 > 8 || q.y1 - q.y0 > 8 || r > 4 * Bt) return false;
     uint64_t m = 0;
     if (o >= kAlphaMin) {
-        const float t = fmaf(2.f * logf(255.f * o), 1.001f, 0.02f);
+        // (the fast log, reciprocals and square roots err by a few ulps, far
+        // inside the margins)
+        const float t = fmaf(2.f * __logf(255.f * o), 1.001f, 0.02f);
         const float bb = B * B;
         const float det = fmaf(A, C, -bb) - fmaf(B, B, -bb);  // A C - B^2
-        const float id = 1.f / det;                            // det(S)
+        const float id = __fdividef(1.f, det);                 // det(S)
         const float sa = C * id, sb = -B * id, sc = A * id;    // S = [[sa, sb], [sb, sc]]
-        const float isc = 1.f / sc;
+        const float isc = __fdividef(1.f, sc);
         const float ky = sb * isc;                             // centre line dx = ky dy
         const float w2 = id * isc;                             // det(S) / Syy
-        const float ry = fmaf(sqrtf(t * sc), 1.001f, 0.01f);   // dy half-extent of the ellipse
-        const float dyr = sb * sqrtf(t / sa);                  // dy of the rightmost point
-        const float fb = (float)Bt;
+        const float ry = fmaf(sqrt_approx(t * sc), 1.001f, 0.01f);  // dy half-extent of the ellipse
+        const float dyr = sb * sqrt_approx(t * __fdividef(1.f, sa));  // dy of the rightmost point
+        const float fb = (float)Bt, ifb = __fdividef(1.f, fb);
         for (int ty = q.y0; ty < q.y1; ++ty) {
             const float yl = fmaf((float)ty, fb, 0.5f) - v;
             const float lo = fmaxf(yl, -ry), hi = fminf(yl + (fb - 1.f), ry);
             if (lo > hi) continue;
             const float d1 = fminf(fmaxf(dyr, lo), hi), d2 = fminf(fmaxf(-dyr, lo), hi);
-            const float xr = fmaf(ky, d1, sqrtf(fmaxf(0.f, w2 * fmaf(-d1 * d1, isc, t))));
-            const float xl = fmaf(ky, d2, -sqrtf(fmaxf(0.f, w2 * fmaf(-d2 * d2, isc, t))));
+            const float xr = fmaf(ky, d1, sqrt_approx(fmaxf(0.f, w2 * fmaf(-d1 * d1, isc, t))));
+            const float xl = fmaf(ky, d2, -sqrt_approx(fmaxf(0.f, w2 * fmaf(-d2 * d2, isc, t))));
             const float eta = fmaf(1e-3f, fabsf(xl) + fabsf(xr), 0.01f);
             // tiles whose pixel-centre columns [tx B + 0.5, tx B + B - 0.5] meet [u + xl, u + xr]
-            const int ta = max(q.x0, (int)ceilf((u + xl - eta - (fb - 0.5f)) / fb));
-            const int tb = min(q.x1 - 1, (int)floorf((u + xr + eta - 0.5f) / fb));
+            const int ta = max(q.x0, (int)ceilf((u + xl - eta - (fb - 0.5f)) * ifb));
+            const int tb = min(q.x1 - 1, (int)floorf((u + xr + eta - 0.5f) * ifb));
             if (ta > tb) continue;
             m |= ((2ull << (tb - ta)) - 1ull) << (8 * (ty - q.y0) + (ta - q.x0));
         }
