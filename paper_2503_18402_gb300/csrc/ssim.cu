@@ -64,24 +64,29 @@ __device__ inline Blk decode(const SViews& sv)
     return b;
 }
 
-// Stage plane[y0 - R .. y0 + T + R) x [x0 - R ..) into s (zero outside the image);
-// a thread's loads are all issued before its first shared store.
+// Stage plane[y0 - R .. y0 + T + R) x [x0 - R ..) into s (zero outside the image).
+// Thread t < 252 keeps column t % 42 and takes the rows t / 42 + 6 k (k < 7),
+// so its column test and offsets are formed once; all of its loads are issued
+// before its first shared store.
+constexpr int SS_SR = SS_THREADS / SS_E;  // staged rows per pass (6)
+static_assert(SS_E % SS_SR == 0, "the staged rows split evenly into passes");
 __device__ inline void stage(const float* __restrict__ plane, int W, int H, int x0, int y0, float (*s)[SS_E + 1])
 {
-    constexpr int N = (SS_E * SS_E + SS_THREADS - 1) / SS_THREADS;
-    float v[N];
+    constexpr int NR = SS_E / SS_SR;
+    const int t = threadIdx.x;
+    if (t >= SS_SR * SS_E) return;
+    const int c = t % SS_E, r0 = t / SS_E;
+    const int x = x0 - SS_R + c;
+    const bool xok = x >= 0 && x < W;
+    const int ys = y0 - SS_R + r0;
+    float v[NR];
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-        const int i = threadIdx.x + k * SS_THREADS;
-        const int r = i / SS_E, c = i % SS_E;
-        const int y = y0 - SS_R + r, x = x0 - SS_R + c;
-        v[k] = (i < SS_E * SS_E && x >= 0 && x < W && y >= 0 && y < H) ? plane[(size_t)y * W + x] : 0.f;
+    for (int k = 0; k < NR; ++k) {
+        const int y = ys + SS_SR * k;
+        v[k] = (xok && y >= 0 && y < H) ? plane[(size_t)y * W + x] : 0.f;
     }
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-        const int i = threadIdx.x + k * SS_THREADS;
-        if (i < SS_E * SS_E) s[i / SS_E][i % SS_E] = v[k];
-    }
+    for (int k = 0; k < NR; ++k) s[r0 + SS_SR * k][c] = v[k];
 }
 
 // Work split of the two window passes: the horizontal pass gives each thread
@@ -243,35 +248,52 @@ k_ssim_bwd(const float* __restrict__ img, const float* __restrict__ tgt, SViews 
 }
 
 // loss[v] = (1 - lam) l1_v + lam (1 - ssim_v); loss[n] = mean over views.
-__global__ void k_ssim_final(const float2* __restrict__ part, SViews sv, float lam, float* __restrict__ loss)
+// One block: the 32 warps split evenly over the views (at least two per
+// view), each warp sums a fixed stride of its view's block partials in FP64,
+// and the warps' sums and then the views' losses are added in a fixed order,
+// so the result does not depend on timing.
+constexpr int SS_FINAL_THREADS = 1024;
+__global__ void __launch_bounds__(SS_FINAL_THREADS)
+k_ssim_final(const float2* __restrict__ part, SViews sv, float lam, float* __restrict__ loss)
 {
-    __shared__ double sm[2][32];
-    double mean = 0.0;
-    for (int v = 0; v < sv.n; ++v) {
-        double s = 0.0, l = 0.0;
-        for (int i = sv.boff[v] + threadIdx.x; i < sv.boff[v + 1]; i += blockDim.x) {
+    constexpr int NW = SS_FINAL_THREADS / 32;
+    __shared__ double sm[2][NW];
+    __shared__ double lv_s[DG_MAX_VIEWS];
+    const int nv = sv.n;
+    const int wpv = NW / nv;  // warps per view
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int v = w / wpv;
+    double s = 0.0, l = 0.0;
+    if (v < nv) {
+        const int step = 32 * wpv;
+        for (int i = sv.boff[v] + 32 * (w % wpv) + lane; i < sv.boff[v + 1]; i += step) {
             const float2 p = part[i];
             s += (double)p.x;
             l += (double)p.y;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s += __shfl_xor_sync(0xffffffffu, s, o);
-            l += __shfl_xor_sync(0xffffffffu, l, o);
-        }
-        if ((threadIdx.x & 31) == 0) { sm[0][threadIdx.x >> 5] = s; sm[1][threadIdx.x >> 5] = l; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double S = 0.0, Lv = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { S += sm[0][w]; Lv += sm[1][w]; }
-            const double n = 3.0 * (double)sv.W[v] * (double)sv.H[v];
-            const double lv = (1.0 - (double)lam) * (Lv / n) + (double)lam * (1.0 - S / n);
-            loss[v] = (float)lv;
-            mean += lv;
-        }
-        __syncthreads();
     }
-    if (threadIdx.x == 0) loss[sv.n] = (float)(mean / sv.n);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        l += __shfl_xor_sync(0xffffffffu, l, o);
+    }
+    if (lane == 0) { sm[0][w] = s; sm[1][w] = l; }
+    __syncthreads();
+    if ((int)threadIdx.x < nv) {
+        const int vv = threadIdx.x;
+        double S = 0.0, Lv = 0.0;
+        for (int q = 0; q < wpv; ++q) { S += sm[0][vv * wpv + q]; Lv += sm[1][vv * wpv + q]; }
+        const double n = 3.0 * (double)sv.W[vv] * (double)sv.H[vv];
+        const double lv = (1.0 - (double)lam) * (Lv / n) + (double)lam * (1.0 - S / n);
+        loss[vv] = (float)lv;
+        lv_s[vv] = lv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mean = 0.0;
+        for (int q = 0; q < nv; ++q) mean += lv_s[q];
+        loss[nv] = (float)(mean / nv);
+    }
 }
 
 }  // namespace
@@ -341,7 +363,7 @@ extern "C" dg_status dg_loss_l1_dssim(const float* img, const float* target, con
     const int nb = sv.boff[sv.n];
     dg::k_ssim_fwd<<<nb, dg::SS_THREADS, 0, s>>>(img, target, sv, win, dm, da, dc, part);
     dg::k_ssim_bwd<<<nb, dg::SS_THREADS, 0, s>>>(img, target, sv, win, dm, da, dc, lambda, dL_dimg);
-    dg::k_ssim_final<<<1, 256, 0, s>>>(part, sv, lambda, loss);
+    dg::k_ssim_final<<<1, dg::SS_FINAL_THREADS, 0, s>>>(part, sv, lambda, loss);
     dg_note_launch(3);
     return dg_check_launch("loss_l1_dssim");
 }
