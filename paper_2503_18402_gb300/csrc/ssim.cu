@@ -265,11 +265,17 @@ k_ssim_final(const float2* __restrict__ part, SViews sv, float lam, float* __res
     const int v = w / wpv;
     double s = 0.0, l = 0.0;
     if (v < nv) {
-        const int step = 32 * wpv;
-        for (int i = sv.boff[v] + 32 * (w % wpv) + lane; i < sv.boff[v + 1]; i += step) {
-            const float2 p = part[i];
-            s += (double)p.x;
-            l += (double)p.y;
+        // eight loads in flight per round, added in index order
+        const int step = 32 * wpv, end = sv.boff[v + 1];
+        for (int i0 = sv.boff[v] + 32 * (w % wpv) + lane; i0 < end; i0 += 8 * step) {
+            float2 p[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) p[u] = i0 + u * step < end ? part[i0 + u * step] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                s += (double)p[u].x;
+                l += (double)p[u].y;
+            }
         }
     }
 #pragma unroll
