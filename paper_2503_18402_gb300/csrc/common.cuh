@@ -142,6 +142,48 @@ __device__ inline bool tile_skip(const float4& a, const float4& b, float px0, fl
     return fmin > 2.f * __logf(255.f * o) + 0.02f;
 }
 
+// Two float32 values in one 64-bit register for the packed float32 operations
+// of sm_100 and later (PTX .f32x2): one instruction does the operation on both
+// halves, each rounded exactly as the scalar operation (fma: one rounding), so
+// packed and scalar code give the same bits.  Low half = first value.
+using f32x2 = unsigned long long;
+
+__device__ __forceinline__ f32x2 f2_pack(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void f2_unpack(f32x2 v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// The two floats at x (8-byte aligned) as one packed register.
+__device__ __forceinline__ f32x2 f2_ld(const float& x) { return *(const f32x2*)&x; }
+
 }  // namespace dg
 
 // Host-side error reporting shared by the C-ABI entry points.
