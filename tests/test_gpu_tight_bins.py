@@ -32,9 +32,10 @@ pytestmark = pytest.mark.gpu
 ALPHA_MIN = 1.0 / 255.0
 
 
-def _run(g, cams, tile, tight, record=0, seed=0):
+def _run(g, cams, tile, tight, record=0, seed=0, mip2d=0.0, bg=(0.0, 0.0, 0.0)):
     """Forward (with per-pixel counts) and full backward of one configuration."""
-    opts = capi.raster_opts(tile=tile, sh_degree=3, split_len=-1, record=record, tight_bins=tight)
+    opts = capi.raster_opts(tile=tile, sh_degree=3, split_len=-1, record=record, tight_bins=tight, mip2d=mip2d,
+                            bg=bg)
     rz = Rasterizer("cuda", opts)
     params = G.gpu_params(g)
     P = g.shape[0]
@@ -86,11 +87,11 @@ def _same_sums(a, b):
     assert not bad.any(), (int(bad.sum()), float((err / (scale + 1e-30)).max()))
 
 
-def _check(g, cams, tile, record=0, min_drop=0.0):
+def _check(g, cams, tile, record=0, min_drop=0.0, mip2d=0.0, bg=(0.0, 0.0, 0.0)):
     P = g.shape[0]
     V = len(cams)
-    t = _run(g, cams, tile, 1, record)
-    p = _run(g, cams, tile, 0, record)
+    t = _run(g, cams, tile, 1, record, mip2d=mip2d, bg=bg)
+    p = _run(g, cams, tile, 0, record, mip2d=mip2d, bg=bg)
     # projection: identical but for the mask words and the count
     np.testing.assert_array_equal(t["radius"], p["radius"])
     np.testing.assert_array_equal(t["depth"].view(np.uint32), p["depth"].view(np.uint32))
@@ -106,7 +107,7 @@ def _check(g, cams, tile, record=0, min_drop=0.0):
     assert t["M"] == int(t["tiles"].sum()) and p["M"] == int(p["tiles"].sum())
     assert t["M"] <= (1.0 - min_drop) * p["M"], (t["M"], p["M"])
     # the oracle's FP64 records of the same float32 parameters
-    k = oracle.consts(tile=tile, sh_degree=3)
+    k = oracle.consts(tile=tile, sh_degree=3, mip2d=mip2d)
     o_feat = [oracle.project(G.f32(g), G.oracle_camera(c), k)["feat"] for c in cams]
     grid = _tile_grid(cams, tile)
     off = np.arange(tile) + 0.5
@@ -182,3 +183,10 @@ def test_textured_tight_lists(textured, tile, record):
 def test_textured_tight_lists_two_views(textured):
     g, cams = textured
     _check(g, [cams[1], cams[5]], 8, 0, min_drop=0.1)
+
+
+def test_textured_tight_lists_mip_filter_and_background(textured):
+    """The 2D filter scales each record's opacity (the mask's threshold follows
+    it); a background colour changes no list."""
+    g, cams = textured
+    _check(g, [cams[2]], 8, 0, min_drop=0.1, mip2d=0.1, bg=(0.2, 0.5, 0.9))
