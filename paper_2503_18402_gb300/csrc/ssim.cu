@@ -181,7 +181,7 @@ k_ssim_fwd(const float* __restrict__ img, const float* __restrict__ tgt, SViews 
     }
 }
 
-__global__ void __launch_bounds__(SS_THREADS)
+__global__ void __launch_bounds__(SS_THREADS, 4)
 k_ssim_bwd(const float* __restrict__ img, const float* __restrict__ tgt, SViews sv, Win win,
            const float* __restrict__ dm, const float* __restrict__ da, const float* __restrict__ dc,
            float lam, float* __restrict__ grad)
@@ -192,6 +192,18 @@ k_ssim_bwd(const float* __restrict__ img, const float* __restrict__ tgt, SViews 
     __shared__ float hs[3][SS_E][SS_T];
     const Blk b = decode(sv);
     const int x0 = b.tx * SS_T, y0 = b.ty * SS_T;
+    // this thread's outputs (column c, rows rb ..): their x and y are loaded
+    // first, so the loads' latency passes during the window sums
+    const int c = threadIdx.x & 31, rb = (threadIdx.x >> 5) * SS_SL;
+    float xo[SS_SL], yo[SS_SL];
+#pragma unroll
+    for (int j = 0; j < SS_SL; ++j) {
+        const int x = x0 + c, y = y0 + rb + j;
+        const bool in = x < b.W && y < b.H;
+        const size_t o = (size_t)b.plane + (size_t)(in ? y : 0) * b.W + (in ? x : 0);
+        xo[j] = in ? img[o] : 0.f;
+        yo[j] = in ? tgt[o] : 0.f;
+    }
     stage(dm + b.plane, b.W, b.H, x0, y0, s0);
     stage(da + b.plane, b.W, b.H, x0, y0, s1);
     stage(dc + b.plane, b.W, b.H, x0, y0, s2);
@@ -215,7 +227,6 @@ k_ssim_bwd(const float* __restrict__ img, const float* __restrict__ tgt, SViews 
         }
     }
     __syncthreads();
-    const int c = threadIdx.x & 31, rb = (threadIdx.x >> 5) * SS_SL;
     // d/dx of the mean over views of (1 - lam) mean|x - y| + lam (1 - mean S)
     const float scale = 1.f / ((float)sv.n * 3.f * (float)b.W * (float)b.H);
     float fs[3][SS_SL];  // filtered partial-derivative maps at this thread's outputs
@@ -239,7 +250,7 @@ k_ssim_bwd(const float* __restrict__ img, const float* __restrict__ tgt, SViews 
         if (x >= b.W || y >= b.H) continue;
         const float f0 = fs[0][j], f1 = fs[1][j], f2 = fs[2][j];
         const size_t o = (size_t)b.plane + (size_t)y * b.W + x;
-        const float xv = img[o], yv = tgt[o];
+        const float xv = xo[j], yv = yo[j];
         const float dS = f0 + 2.f * xv * f1 + yv * f2;
         const float d = xv - yv;
         const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
