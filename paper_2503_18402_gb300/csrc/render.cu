@@ -1177,13 +1177,17 @@ k_render_fwd_w(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
         if (T < kTMin) done = true;
     }
     bool alldone = __all_sync(0xffffffffu, done);
+    // the Gaussian indices of a batch are loaded one batch ahead, so a batch
+    // waits only for its records
+    uint32_t gn = lo + lane < hi ? gid[rg.x + lo + lane] : 0u;
     for (int base = lo; base < hi && !alldone; base += 32) {
         const int j = base + lane;
+        const uint32_t g = gn;
+        gn = j + 32 < hi ? gid[rg.x + j + 32] : 0u;
         bool keep = false;
         float4 ga, gb;
         float gc = 0.f;
         if (j < hi) {
-            const uint32_t g = gid[rg.x + j];
             load_record<REC>(feat, g, ga, gb, gc);
             keep = !tile_skip(ga, gb, bx0, bx1, by0, by1);
         }
