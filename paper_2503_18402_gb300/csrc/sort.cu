@@ -159,27 +159,27 @@ k_emit(const float4* __restrict__ feat, const int* __restrict__ radius, const ui
         const long long end = (base + RS_TILE) < M ? (base + RS_TILE) : M;
         const int s_lo = bstart[blockIdx.x];
         // stage the Gaussians whose pair range starts before `end` (a prefix of
-        // s_lo, s_lo + 1, ...).  Each link of the load chain (pair offset ->
-        // record index -> record) is issued for all of a thread's candidates at
-        // once; the second half of the candidates only when the block holds
-        // more than RS_TILE / 2 Gaussians (fewer than 4 pairs each).
+        // s_lo, s_lo + 1, ...).  A candidate's pair offset and record index are
+        // loaded together (both follow from its sorted position), then its
+        // record; each link is issued for all of a thread's candidates at once,
+        // the second half of the candidates only when the block holds more
+        // than RS_TILE / 2 Gaussians (fewer than 4 pairs each).
         constexpr int HALF = RS_IPT / 2;
         long long st[RS_IPT];
+        uint32_t gk[RS_IPT];
 #pragma unroll
         for (int k = 0; k < HALF; ++k) {
             const long long s = (long long)s_lo + threadIdx.x + k * RS_THREADS;
             st[k] = s < P ? (long long)poff[s] : LLONG_MAX;
+            gk[k] = s < P ? order[s] : 0u;
         }
         const bool more = __syncthreads_or(st[HALF - 1] < end) != 0;
 #pragma unroll
         for (int k = HALF; k < RS_IPT; ++k) {
             const long long s = (long long)s_lo + threadIdx.x + k * RS_THREADS;
             st[k] = more && s < P ? (long long)poff[s] : LLONG_MAX;
+            gk[k] = more && s < P ? order[s] : 0u;
         }
-        uint32_t gk[RS_IPT];
-#pragma unroll
-        for (int k = 0; k < RS_IPT; ++k)
-            gk[k] = st[k] < end ? order[(long long)s_lo + threadIdx.x + k * RS_THREADS] : 0u;
         int top = 0;
 #pragma unroll
         for (int k = 0; k < RS_IPT; ++k) {
