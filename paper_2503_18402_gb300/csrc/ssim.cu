@@ -13,7 +13,8 @@
 //
 // Two passes over 32 x 32 output tiles (256 threads, 4 rows each): the
 // forward stages the tile and a 5-pixel halo of x and y in shared memory,
-// runs the horizontal then the vertical 11-tap sums of the five statistics,
+// runs the horizontal then the vertical 11-tap sums of four statistics (mu_x,
+// mu_y, a + b, c: S uses a and b only through their sum),
 // and writes the three partial-derivative maps plus per-block sums of S and
 // |x - y|; the backward stages the maps with their halo, filters them the same
 // way and writes dL/dx including the L1 term.  A last one-block kernel sums
@@ -101,7 +102,9 @@ k_ssim_fwd(const float* __restrict__ img, const float* __restrict__ tgt, SViews 
 {
     __shared__ float sx[SS_E][SS_E + 1];
     __shared__ float sy[SS_E][SS_E + 1];
-    __shared__ float hs[5][SS_E][SS_T];  // horizontal sums: mu_x, mu_y, a, b, c
+    // horizontal sums: mu_x, mu_y, a + b, c (S needs E[x^2] and E[y^2] only
+    // through their sum, so one window sum serves both)
+    __shared__ float hs[4][SS_E][SS_T];
     __shared__ float red[2][SS_THREADS / 32];
     const Blk b = decode(sv);
     const int x0 = b.tx * SS_T, y0 = b.ty * SS_T;
@@ -116,26 +119,25 @@ k_ssim_fwd(const float* __restrict__ img, const float* __restrict__ tgt, SViews 
         for (int q = 0; q < SS_SL + 2 * SS_R; ++q) { xv[q] = sx[r][c0 + q]; yv[q] = sy[r][c0 + q]; }
 #pragma unroll
         for (int o = 0; o < SS_SL; ++o) {
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
             for (int k = 0; k <= 2 * SS_R; ++k) {
                 const float x = xv[o + k], y = yv[o + k], w = win.w[k];
                 s0 = fmaf(w, x, s0);
                 s1 = fmaf(w, y, s1);
-                s2 = fmaf(w, x * x, s2);
-                s3 = fmaf(w, y * y, s3);
-                s4 = fmaf(w, x * y, s4);
+                s2 = fmaf(w, fmaf(x, x, y * y), s2);
+                s3 = fmaf(w, x * y, s3);
             }
             hs[0][r][c0 + o] = s0; hs[1][r][c0 + o] = s1; hs[2][r][c0 + o] = s2;
-            hs[3][r][c0 + o] = s3; hs[4][r][c0 + o] = s4;
+            hs[3][r][c0 + o] = s3;
         }
     }
     __syncthreads();
     // vertical pass: lane = column, warp w = output rows SS_SL w .. SS_SL w + SS_SL - 1
     const int c = threadIdx.x & 31, rb = (threadIdx.x >> 5) * SS_SL;
-    float st[5][SS_SL];  // window sums of the five statistics at this thread's outputs
+    float st[4][SS_SL];  // window sums of the four statistics at this thread's outputs
 #pragma unroll
-    for (int t = 0; t < 5; ++t) {
+    for (int t = 0; t < 4; ++t) {
         float col[SS_SL + 2 * SS_R];
 #pragma unroll
         for (int q = 0; q < SS_SL + 2 * SS_R; ++q) col[q] = hs[t][rb + q][c];
@@ -153,11 +155,11 @@ k_ssim_fwd(const float* __restrict__ img, const float* __restrict__ tgt, SViews 
         const int r = rb + j;
         const int x = x0 + c, y = y0 + r;
         if (x >= b.W || y >= b.H) continue;
-        const float mx = st[0][j], my = st[1][j], a = st[2][j], bb = st[3][j], cc = st[4][j];
+        const float mx = st[0][j], my = st[1][j], ab = st[2][j], cc = st[3][j];
         const float A1 = 2.f * mx * my + kC1;
         const float A2 = 2.f * (cc - mx * my) + kC2;
         const float B1 = mx * mx + my * my + kC1;
-        const float B2 = (a - mx * mx) + (bb - my * my) + kC2;
+        const float B2 = (ab - mx * mx - my * my) + kC2;
         const float inv = 1.f / (B1 * B2);
         const float S = A1 * A2 * inv;
         const size_t o = (size_t)b.plane + (size_t)y * b.W + x;
