@@ -1142,7 +1142,9 @@ k_render_bwd_ep(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
 // launch, and each entry some pixel of the block blended gets bit 7 and the
 // block's bit OR-ed into its byte (one 32-bit atomic OR per entry and block).
 template <bool PROD, int REC>
-__global__ void __launch_bounds__(64)
+// (16 blocks of 64 threads per SM, 64 registers: 0.366 -> 0.353 ms against the
+// compiler's 56-register choice of 18 blocks)
+__global__ void __launch_bounds__(64, 16)
 k_render_fwd_w(const void* __restrict__ feat, const uint32_t* __restrict__ gid,
                const uint2* __restrict__ ranges, RViews rv, RHdr* hdr, const int4* __restrict__ items,
                const int4* __restrict__ sitems, Slots sl, uint8_t* __restrict__ flags, long long flags_cap,
