@@ -479,7 +479,8 @@ def run_ours(args):
         ach = units / dur_s / 1e9
         out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                            "frac": round(ach / hbm, 4), "traffic": measured_traffic(dom),
-                           "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800 GB/s"}
+                           "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks
+                           else "fallback 6800 GB/s"}
     # every timed stage against its bound: HBM stages by algorithmic bytes, the
     # compositing passes by FP32 work (both counts: the per-examined-entry count
     # and the count of the operations the algorithm needs per walked/blended entry)
