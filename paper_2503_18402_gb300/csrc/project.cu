@@ -283,8 +283,14 @@ __device__ inline bool tile_mask(float u, float v, float A, float B, float C, fl
 #ifndef DG_PROJECT_FWD_MINB
 #define DG_PROJECT_FWD_MINB 5
 #endif
-template <int NB>
-__global__ void __launch_bounds__(128, DG_PROJECT_FWD_MINB)
+#ifndef DG_PROJECT_FWD_MINB_LATE
+#define DG_PROJECT_FWD_MINB_LATE 8
+#endif
+// LATE_SH (one view per launch): the colour coefficients are loaded where the
+// colour is formed instead of before the view loop, so they are not live
+// across the projection and the kernel fits more resident warps.
+template <int NB, bool LATE_SH>
+__global__ void __launch_bounds__(128, LATE_SH ? DG_PROJECT_FWD_MINB_LATE : DG_PROJECT_FWD_MINB)
 k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs_host, const dg_camera* cdev, int B,
               float near_plane, float eps2d, float mip2d, int tight, float4* __restrict__ feat, float* __restrict__ depth,
               int* __restrict__ radius, int* __restrict__ tiles, uint8_t* __restrict__ clampm)
@@ -296,10 +302,12 @@ k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs
     G3 g;
     gauss3d(prm, stride, i, g);
     float sh[NB][3];
+    if (!LATE_SH) {
 #pragma unroll
-    for (int k = 0; k < NB; ++k)
+        for (int k = 0; k < NB; ++k)
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) sh[k][ch] = prm[(11 + 3 * k + ch) * stride + i];
+            for (int ch = 0; ch < 3; ++ch) sh[k][ch] = prm[(11 + 3 * k + ch) * stride + i];
+    }
     const float osig = 1.f / (1.f + expf(-prm[10 * stride + i]));
     for (int v = 0; v < vs.n; ++v) {
         const Cam& cam = vs.cam[v];
@@ -329,7 +337,8 @@ k_project_fwd(const float* __restrict__ prm, long long stride, int P, ViewSet vs
                     for (int ch = 0; ch < 3; ++ch) {
                         float acc = 0.f;
 #pragma unroll
-                        for (int k = 0; k < NB; ++k) acc += Y[k] * sh[k][ch];
+                        for (int k = 0; k < NB; ++k)
+                            acc += Y[k] * (LATE_SH ? prm[(11 + 3 * k + ch) * stride + i] : sh[k][ch]);
                         acc += 0.5f;
                         if (acc < 0.f) { cm |= (uint8_t)(1u << ch); acc = 0.f; }
                         col[ch] = acc;
@@ -736,11 +745,17 @@ extern "C" dg_status dg_project(const float* params, int64_t stride, int64_t P, 
     const int threads = 128;
     const int blocks = (int)((P + threads - 1) / threads);
     cudaStream_t s = (cudaStream_t)stream;
+    const int tight = opts->tight_bins ? 1 + (opts->record == 1) : 0;
+    auto go = [&](auto kern) {
+        kern<<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane,
+                                        opts->eps2d, opts->mip2d, tight, (float4*)feat, depth, radius, tiles, clamp);
+    };
+    const bool one = n_views == 1;
     switch (opts->sh_degree) {
-    case 0: dg::k_project_fwd<1><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, opts->mip2d, opts->tight_bins ? 1 + (opts->record == 1) : 0, (float4*)feat, depth, radius, tiles, clamp); break;
-    case 1: dg::k_project_fwd<4><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, opts->mip2d, opts->tight_bins ? 1 + (opts->record == 1) : 0, (float4*)feat, depth, radius, tiles, clamp); break;
-    case 2: dg::k_project_fwd<9><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, opts->mip2d, opts->tight_bins ? 1 + (opts->record == 1) : 0, (float4*)feat, depth, radius, tiles, clamp); break;
-    default: dg::k_project_fwd<16><<<blocks, threads, 0, s>>>(params, (long long)stride, (int)P, vs, cams_dev, opts->tile, opts->near_plane, opts->eps2d, opts->mip2d, opts->tight_bins ? 1 + (opts->record == 1) : 0, (float4*)feat, depth, radius, tiles, clamp); break;
+    case 0: one ? go(dg::k_project_fwd<1, true>) : go(dg::k_project_fwd<1, false>); break;
+    case 1: one ? go(dg::k_project_fwd<4, true>) : go(dg::k_project_fwd<4, false>); break;
+    case 2: one ? go(dg::k_project_fwd<9, true>) : go(dg::k_project_fwd<9, false>); break;
+    default: one ? go(dg::k_project_fwd<16, true>) : go(dg::k_project_fwd<16, false>); break;
     }
     dg_note_launch();
     return dg_check_launch("project_fwd");
